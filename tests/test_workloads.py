@@ -1,0 +1,57 @@
+"""Shape checks of the seeded input generators (CPU only)."""
+import numpy as np
+
+from paper_2501_13051_gb300 import workloads as W
+
+
+def test_splitmix_counter_form_matches_sequential_form():
+    # sequential SplitMix64: state += gamma; output = mix(state)
+    def seq(seed, k):
+        m = (1 << 64) - 1
+        s, out = seed, []
+        for _ in range(k):
+            s = (s + 0x9E3779B97F4A7C15) & m
+            z = s
+            z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+            z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+            out.append(z ^ (z >> 31))
+        return out
+    got = W.splitmix64(np.uint64(12345), np.arange(6, dtype=np.uint64))
+    assert [int(v) for v in got] == seq(12345, 6)
+
+
+def test_er_graph_shape():
+    e = W.er_graph(1000, 1500, 1)
+    assert e.shape == (1500, 2) and e.dtype == np.uint32
+    assert (e[:, 0] != e[:, 1]).all()
+    assert len({tuple(r) for r in e.tolist()}) == 1500
+    assert np.array_equal(e, W.er_graph(1000, 1500, 1))
+
+
+def test_forest_shape():
+    n = 20000
+    f = W.random_forest(n, 2)
+    tree, cross = f[: len(f) - n // 50], f[len(f) - n // 50:]
+    assert (tree[:, 0] < tree[:, 1]).all()            # parent drawn from earlier nodes
+    assert len(np.unique(tree[:, 1])) == len(tree)     # one parent per child
+    assert 0.97 < len(tree) / (n - 1) < 0.99
+    assert len(cross) == n // 50 and (cross[:, 0] != cross[:, 1]).all()
+    assert len({tuple(r) for r in f.tolist()}) == len(f)
+
+
+def test_points_to_and_owl_shapes():
+    edb = W.points_to_edb(1 / 1024, 3)
+    assert set(edb) == {"assign", "dereference"}
+    assert edb["assign"].shape[1] == 2 and len(edb["assign"]) <= 4_000_000 // 1024
+    tri, sch = W.owl_triples(20000, 4, n_entities=5000, n_classes=60)
+    assert len(sch.sub_prop) == 40 and len(sch.transitive) == 10
+    assert len(sch.domain) == 60 and len(sch.range_) == 60 and len(sch.inverse) == 10
+    assert tri["type"][:, 1].min() >= 5000
+    prog = W.owl_program(tri, sch)
+    assert len(prog.rules) == 3 + 40 + 10 + 60 + 60 + 20
+
+
+def test_batched_sizes_log_uniform():
+    s = W.batched_graph_sizes(512, 5)
+    assert s.min() >= 1000 and s.max() <= 500000
+    assert 0.3 < np.mean(np.log(s) < np.log(np.sqrt(1e3 * 5e5))) < 0.7
