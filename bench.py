@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the semi-naive Datalog fixpoint on GB300.
+
+One step = one complete fixpoint (every round: hash index, three-pass join,
+radix sort + dedup, difference + merge) of the same-generation program on a
+seeded random forest of 200,000 nodes (each node's parent uniform among the
+earlier nodes with probability 0.98, else a root) plus 2% random cross
+edges, with the input edge columns already resident in device memory.
+Metric: derived tuples per second (sum of the derived relation's size over
+the steps / device time of the steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun each rank runs an independent instance (seed + rank): the
+fixpoint has no exchange step here, so ranks are replicas and the value is
+the tuples all ranks derived / the slowest rank's time.
+
+Also reported: an end-to-end figure through the C ABI with host buffers
+(edge upload and export of the whole derived relation inside the timed
+region), the roofline of the dominant kernel (its algorithmic bytes / its
+CUDA-event time over the timed steps, against the measured HBM copy
+bandwidth), and the CPU oracle timed on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2501_13051_gb300 import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    "sg-forest-200k": dict(kind="sg", n=200_000, seed=2,
+                           desc="same-generation on a random forest, 200000 nodes, "
+                                "p_parent 0.98, +2% cross edges"),
+    "tc-er-1000-1500": dict(kind="tc", n=1000, m=1500, seed=1,
+                            desc="transitive closure on a directed Erdos-Renyi graph, "
+                                 "1000 nodes, 1500 edges"),
+}
+# bounded sample of the default workload for the CPU oracle (seconds of work)
+ORACLE_SAMPLE = dict(kind="sg", n=10_000, seed=2)
+METRIC = "derived tuples/s per fixpoint"
+
+
+def make_program(spec, seed_offset=0):
+    seed = spec["seed"] + seed_offset
+    if spec["kind"] == "sg":
+        return W.sg_program(W.random_forest(spec["n"], seed))
+    return W.tc_program(W.er_graph(spec["n"], spec["m"], seed))
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s, one earlier GB300 measurement)"
+
+
+def kernel_traffic(name):
+    """DRAM bytes per unit for a kernel from the committed ncu summary, or
+    None when the kernel's source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))[name]
+        src = os.path.join(ROOT, "paper_2501_13051_gb300", "csrc", d["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d["source_sha"]:
+            return None
+        return d
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons while the timed steps run."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_oracle_sample(spec):
+    from oracle import oracle as orc
+    prog = make_program(spec)
+    t = time.perf_counter()
+    res = orc.run_program(prog)
+    dt = time.perf_counter() - t
+    return res.derived(prog), dt
+
+
+def bench_reference(args, rank, world):
+    """Reference arm: the CPU oracle, as it stands, on a bounded sample of the
+    workload per step, on this host's cores (rank 0 only)."""
+    if rank != 0:
+        return
+    spec = ORACLE_SAMPLE
+    for _ in range(args.warmup):
+        run_oracle_sample(spec)
+    derived, secs = 0, 0.0
+    for _ in range(args.steps):
+        d, dt = run_oracle_sample(spec)
+        derived += d
+        secs += dt
+    v = derived / secs
+    sample = (f"same-generation, forest {spec['n']} nodes (+2% cross edges), seed {spec['seed']}: "
+              f"{derived // max(args.steps, 1)} tuples per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "tuples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "tuples/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "tuples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def bench_gb300(args, rank, world, dist):
+    import torch
+    from paper_2501_13051_gb300 import cdl
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    spec = WORKLOADS[args.workload]
+    prog = make_program(spec, seed_offset=rank)
+    edges = prog.edb["edge"]
+    head = "sg" if spec["kind"] == "sg" else "path"
+    dev_cols = [torch.from_numpy(np.ascontiguousarray(edges[:, k]).view(np.int32)).cuda()
+                for k in range(2)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(timing):
+        with cdl.Engine(timing=timing) as e:
+            e.relation("edge", 2)
+            e.relation(head, 2)
+            e.load("edge", dev_cols)
+            for r in prog.rules:
+                e.rule(r.head, r.body, r.neq)
+            st = e.run()
+            return st, (e.kernel_profile() if timing else None)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(False)
+    # ---- timed steps (device resident input), kernels timed per class
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    derived, launches, rounds = 0, 0, 0
+    prof = {}
+    for i in range(args.steps):
+        if i:
+            flush.fill_(i & 0xFF)  # evict L2 between steps
+        st, pr = step(True)
+        derived += st.derived_tuples
+        launches += st.kernel_launches
+        rounds = st.iterations
+        for p in pr:
+            q = prof.setdefault(p["kernel"], {"launches": 0, "ms": 0.0, "bytes": 0.0})
+            q["launches"] += p["launches"]
+            q["ms"] += p["ms"]
+            q["bytes"] += p["bytes"]
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    secs = ev0.elapsed_time(ev1) * 1e-3
+    if dist is not None:
+        t = torch.tensor([secs, float(derived)], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        secs, derived = float(mx[0]), int(t[1])
+    value = derived / secs
+
+    # ---- end to end through the C ABI with host buffers
+    pinned_in = [torch.from_numpy(np.ascontiguousarray(edges[:, k]).view(np.int32)).pin_memory()
+                 for k in range(2)]
+    n_out = st.derived_tuples
+    pinned_out = [torch.empty(max(n_out, 1), dtype=torch.int32, pin_memory=True) for _ in range(2)]
+
+    def step_e2e():
+        with cdl.Engine() as e:
+            e.relation("edge", 2)
+            e.relation(head, 2)
+            e.load("edge", pinned_in)
+            for r in prog.rules:
+                e.rule(r.head, r.body, r.neq)
+            s = e.run()
+            e.export(head, out=[t.data_ptr() for t in pinned_out])
+            return s
+
+    step_e2e()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    d_e2e = 0
+    for _ in range(args.steps):
+        d_e2e += step_e2e().derived_tuples
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    secs_e2e = e0.elapsed_time(e1) * 1e-3
+    e2e = {"value": d_e2e * world / secs_e2e, "unit": "tuples/s",
+           "h2d_bytes_per_step": int(edges.shape[0] * 8), "d2h_bytes_per_step": int(n_out * 8)}
+
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel class
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, d = dom
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+    peak, peak_src = measured_peak()
+    tr = kernel_traffic(name)
+    traffic = None
+    if tr is not None:
+        traffic = tr["dram_bytes_per_unit"] * (d["bytes"] / d["launches"]) / tr["algo_bytes_per_unit"]
+    total_ms = sum(v["ms"] for v in prof.values())
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": name,
+                "kernel_share": d["ms"] / total_ms, "launches": d["launches"],
+                "peak_source": peak_src}
+    # ---- the oracle on a bounded sample, on this host's cores
+    od, osecs = run_oracle_sample(ORACLE_SAMPLE)
+    cpu = {"value": od / osecs, "unit": "tuples/s", "cores": 1, "kind": "oracle",
+           "sample": f"same-generation, forest {ORACLE_SAMPLE['n']} nodes (+2% cross edges), "
+                     f"seed {ORACLE_SAMPLE['seed']}: {od} tuples in {osecs:.2f} s, 1 thread "
+                     f"of {os.cpu_count()} host cores"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "tuples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": spec["desc"],
+                   "edges": int(edges.shape[0]), "derived_per_step": int(st.derived_tuples),
+                   "iterations": int(rounds), "seed": spec["seed"],
+                   "l2": "256 MB buffer written between steps; working set > L2",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+        "clocks": clocks,
+        "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                        "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="sg-forest-200k", choices=sorted(WORKLOADS))
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        bench_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    try:
+        bench_gb300(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

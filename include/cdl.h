@@ -1,0 +1,249 @@
+/*
+ * cdl.h -- C ABI of a column-oriented Datalog engine for one GB300 GPU.
+ *
+ * The engine evaluates positive Horn rules H <- B1, ..., Bn (Section 2 of
+ * "Column-Oriented Datalog on the GPU") to their least fixpoint.  Relations
+ * are stored column-wise: one uint32 array per attribute (Section 3, the
+ * decomposed storage model, with the row index as the surrogate id).  Each
+ * round of the semi-naive loop (Section 3, full / delta / new versions, all
+ * rules per round) runs four steps on the GPU:
+ *   (a) an open-addressing hash index over the distinct values of a join
+ *       column, key -> (start, count) in the relation sorted by that column
+ *       (Section 3, hybrid index);
+ *   (b) a join in three passes -- count each probe row's range, exclusive
+ *       scan, output-partitioned write of the head columns (Algorithm 1);
+ *   (c) LSD radix sort of the new tuples and removal of repeats (Section 5:
+ *       per-column radix sorting);
+ *   (d) set difference new - full and eager merge of the difference into the
+ *       sorted full relation (Section 4, "Union and Deduplication"; Section
+ *       3, "Continuous Memory Layout").
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a cdl_status; nothing aborts, asserts or traps.
+ *     On error, cdl_last_error(engine) describes it (engine calls only).
+ *   - Values are uint32; 0xFFFFFFFF is reserved (it marks empty hash slots)
+ *     and is rejected on load with CDL_E_VALUE.
+ *   - Relations are sets; loading repeats is allowed and they are dropped.
+ *   - Exported tuples are unique and ordered lexicographically by unsigned
+ *     column value, column 0 first.
+ *   - Counts and offsets are 64-bit.  A single relation holds fewer than
+ *     2^32 tuples (CDL_E_CAPACITY otherwise).
+ *   - Arity is 1..CDL_MAX_ARITY.
+ *   - "stream" arguments are cudaStream_t values passed as void*; NULL means
+ *     the legacy default stream.  Device pointers must be 16-byte aligned.
+ *   - The caller owns every buffer it passes; the library copies what it
+ *     keeps.  Device memory the engine keeps comes from the caller's
+ *     allocator callbacks when given, else from cudaMalloc.
+ */
+#ifndef CDL_H_
+#define CDL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CDL_MAX_ARITY 4
+#define CDL_MAX_BODY 4
+#define CDL_EMPTY_KEY 0xFFFFFFFFu
+
+typedef enum {
+  CDL_OK = 0,
+  CDL_E_INVALID = -1,  /* bad argument, unsupported rule shape */
+  CDL_E_NOMEM = -2,    /* allocator returned NULL or the memory limit is reached */
+  CDL_E_CAPACITY = -3, /* an output buffer or a 2^32 size limit is too small */
+  CDL_E_VALUE = -4,    /* input holds the reserved value 0xFFFFFFFF */
+  CDL_E_MAXITER = -5,  /* the fixpoint needs more rounds than max_iters */
+  CDL_E_TIMEOUT = -6,  /* a bounded device-side wait ran out */
+  CDL_E_CUDA = -7,     /* a CUDA runtime call failed */
+  CDL_E_STATE = -8     /* call not valid in the engine's current state */
+} cdl_status;
+
+/* ------------------------------------------------------------------------ */
+/* Engine                                                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct cdl_engine cdl_engine; /* opaque, owned by the library */
+typedef uint32_t cdl_rel;
+
+/* Device allocator supplied by the caller (e.g. backed by PyTorch).  alloc
+ * returns a device pointer (>= 256-byte aligned) or NULL; free returns it. */
+typedef void* (*cdl_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*cdl_free_fn)(void* ptr, size_t bytes, void* ctx);
+
+typedef struct {
+  cdl_alloc_fn alloc;  /* NULL: the engine uses cudaMalloc / cudaFree */
+  cdl_free_fn free;
+  void* alloc_ctx;
+  void* stream;        /* cudaStream_t every kernel of the engine runs on */
+  uint64_t mem_limit;  /* bytes of device memory the engine may hold; 0 = no limit */
+  uint64_t max_iters;  /* rounds that may produce new tuples; 0 = no limit */
+  uint64_t spin_limit; /* iterations of any device-side wait; 0 = default (2^26) */
+  uint32_t timing;     /* 1: time every kernel launch with CUDA events */
+  int32_t estimator;   /* join-size estimator: 0 off, 1 on, 2 on + log join stats */
+  double hash_load;    /* hash table load factor in (0, 0.9]; 0 = default 0.5 */
+  uint32_t radix_bits; /* radix digit width 4..8; 0 = default 8 */
+  const char* log_path; /* join statistics log (estimator == 2); NULL = none */
+} cdl_options;
+
+/* Fills *opts with the defaults (everything zero / NULL except the
+ * defaults stated above). */
+void cdl_options_default(cdl_options* opts);
+
+/* Creates an engine on the current CUDA device.  Section 2: a program is a
+ * set of rules over input (EDB) and derived (IDB) relations. */
+cdl_status cdl_create(const cdl_options* opts, cdl_engine** out);
+
+/* Frees everything the engine holds.  NULL is accepted. */
+cdl_status cdl_destroy(cdl_engine* e);
+
+/* Declares a relation of the given arity (Section 3: n-ary relations stored
+ * as one column per attribute).  Names are unique. */
+cdl_status cdl_relation_create(cdl_engine* e, const char* name, uint32_t arity, cdl_rel* out);
+
+/* Adds n tuples to relation rel: cols[k] points to n uint32 values of column
+ * k (host memory if on_device == 0, device memory otherwise).  The library
+ * copies the values; repeats are dropped.  Must precede cdl_run.
+ * Returns CDL_E_VALUE if a value is 0xFFFFFFFF (nothing is added then). */
+cdl_status cdl_relation_load(cdl_engine* e, cdl_rel rel, const uint32_t* const* cols,
+                             uint64_t n, int on_device);
+
+typedef struct {
+  uint32_t is_const; /* 0: variable, 1: constant */
+  uint32_t v;        /* variable id (any small integer) or constant value */
+} cdl_term;
+
+typedef struct {
+  cdl_rel rel;
+  uint32_t arity;
+  const cdl_term* terms; /* arity terms */
+} cdl_atom;
+
+/* A Horn rule head <- body[0], ..., body[nbody-1], with nneq inequalities
+ * neq[2i] != neq[2i+1] between variable ids (the x != y of Section 5.2).
+ * Every head variable must occur in the body, bodies have 1..CDL_MAX_BODY
+ * atoms, and consecutive atoms of the join order must share a variable.
+ * The rule is lowered to copy / join / project plans (Section 4). */
+typedef struct {
+  cdl_atom head;
+  uint32_t nbody;
+  const cdl_atom* body;
+  uint32_t nneq;
+  const uint32_t* neq;
+} cdl_rule;
+
+cdl_status cdl_rule_add(cdl_engine* e, const cdl_rule* rule);
+
+typedef struct {
+  uint64_t iterations;     /* rounds that produced a new tuple */
+  uint64_t rounds;         /* rounds executed (the last found nothing new) */
+  uint64_t derived_tuples; /* sum over derived relations of their size */
+  double seconds;          /* device time of the run (CUDA events) */
+  double algo_bytes;       /* bytes the steps must move (see the design notes) */
+  uint64_t joins;          /* join operations executed */
+  uint64_t kernel_launches;
+  uint64_t est_predictions; /* joins sized by the estimator */
+  uint64_t est_overflows;   /* of those, joins that fell back to the exact count */
+  uint64_t* delta_per_round; /* caller array or NULL: new tuples per round */
+  uint64_t delta_cap;        /* its length */
+} cdl_stats;
+
+/* Runs the semi-naive loop to the fixpoint on the engine's stream and waits
+ * for it.  CDL_E_MAXITER if more than max_iters rounds produce tuples.
+ * Rules may not be added afterwards (CDL_E_STATE). */
+cdl_status cdl_run(cdl_engine* e, cdl_stats* stats);
+
+/* Number of tuples of rel (after loads or a run). */
+cdl_status cdl_relation_size(cdl_engine* e, cdl_rel rel, uint64_t* n);
+
+/* Copies rel's tuples, sorted and unique, into cols[k] (cap tuples each;
+ * host memory if on_device == 0).  *n_written receives the size; a cap
+ * below the size gives CDL_E_CAPACITY and writes nothing. */
+cdl_status cdl_relation_export(cdl_engine* e, cdl_rel rel, uint32_t* const* cols, uint64_t cap,
+                               uint64_t* n_written, int on_device);
+
+/* Per-kernel timing gathered while options.timing == 1: for kernel class
+ * idx (0..), its name, launches, summed device milliseconds and summed
+ * algorithmic bytes.  CDL_E_INVALID when idx is past the last class. */
+cdl_status cdl_kernel_profile(cdl_engine* e, uint32_t idx, char* name, size_t name_cap,
+                              uint64_t* launches, double* ms, double* bytes);
+
+/* Engine-owned description of the last error; valid until the next call. */
+const char* cdl_last_error(const cdl_engine* e);
+
+/* ------------------------------------------------------------------------ */
+/* Steps of one round on caller-owned device buffers                          */
+/* ------------------------------------------------------------------------ */
+/* These run exactly the kernels the engine uses, on plain device pointers.
+ * Scratch memory comes from the caller: each call with workspace == NULL
+ * only reports the bytes it needs in *ws_bytes and returns CDL_OK. */
+
+/* Bytes of a hash table for n_keys distinct keys at load factor load
+ * (slots are 16 bytes, the slot count a power of two). */
+uint64_t cdl_hash_table_bytes(uint64_t n_keys, double load);
+
+/* Step (a), Section 3 hybrid index.  keys: n values sorted ascending.  For
+ * every distinct value v the table receives (v, start, count): the first
+ * position of v in keys and its run length.  table_bytes must be at least
+ * cdl_hash_table_bytes(n, load) for some load <= 0.9 (so that every key
+ * finds a slot); CDL_E_INVALID otherwise. */
+cdl_status cdl_hash_build(const uint32_t* keys, uint64_t n, void* table, uint64_t table_bytes,
+                          void* stream);
+
+/* Step (b) first pass, Algorithm 1 probe loop: counts[i] = number of
+ * occurrences of probe[i] in the table's column (0 if absent). */
+cdl_status cdl_join_count(const uint32_t* probe, uint64_t n, const void* table,
+                          uint64_t table_bytes, uint32_t* counts, void* stream);
+
+/* Step (b) second pass: out[i] = sum of in[0..i) in 64 bits; *total_host
+ * (host pointer, may be NULL) receives the sum of all n (the call then waits
+ * for the stream). */
+cdl_status cdl_exclusive_scan(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* total_host,
+                              void* workspace, size_t* ws_bytes, void* stream);
+
+/* Where a head column of a join takes its value from. */
+typedef struct {
+  uint32_t side; /* 0: probe row column, 1: build row column, 2: constant */
+  uint32_t v;    /* column index, or the constant */
+} cdl_colref;
+
+/* Step (b) complete (hash build on the build side + count + scan + write,
+ * Algorithm 1 with output partitioning, projection fused).  The build side
+ * must be sorted by build_cols[build_key].  For every probe row p and build
+ * row b with probe_cols[probe_key][p] == build_cols[build_key][b] and
+ * column(neq[2i]) != column(neq[2i+1]) for every inequality, one output
+ * tuple out[k] = value of spec[k] is written.  Without inequalities the
+ * output is in Algorithm 1's order (probe row, then build position); with
+ * them, surviving tuples are packed in an unspecified order.  *n_out
+ * receives the tuple count; out_cap below the unfiltered join size gives
+ * CDL_E_CAPACITY with *n_out = that size and nothing written. */
+cdl_status cdl_join(const uint32_t* const* probe_cols, uint32_t probe_arity, uint64_t n_probe,
+                    uint32_t probe_key, const uint32_t* const* build_cols, uint32_t build_arity,
+                    uint64_t n_build, uint32_t build_key, const cdl_colref* spec, uint32_t out_arity,
+                    const cdl_colref* neq, uint32_t nneq, uint32_t* const* out_cols,
+                    uint64_t out_cap, uint64_t* n_out, void* workspace, size_t* ws_bytes,
+                    void* stream);
+
+/* Step (c): sorts n tuples of arity columns lexicographically (LSD radix
+ * sort, stable), drops repeats, writes the unique tuples to out_cols and
+ * their number to *n_out.  cols are left unchanged. */
+cdl_status cdl_sort_unique(const uint32_t* const* cols, uint32_t arity, uint64_t n,
+                           uint32_t* const* out_cols, uint64_t* n_out, void* workspace,
+                           size_t* ws_bytes, void* stream);
+
+/* Step (d): full (n_full tuples) is sorted and unique; fresh (n_fresh tuples)
+ * is sorted, repeats allowed.  Writes delta = fresh - full (sorted, unique,
+ * *n_delta tuples) and merged = full U delta (sorted, n_full + *n_delta
+ * tuples).  merged must hold n_full + n_fresh tuples, delta n_fresh. */
+cdl_status cdl_diff_merge(const uint32_t* const* full, uint64_t n_full,
+                          const uint32_t* const* fresh, uint64_t n_fresh, uint32_t arity,
+                          uint32_t* const* delta, uint64_t* n_delta, uint32_t* const* merged,
+                          void* workspace, size_t* ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDL_H_ */

@@ -25,6 +25,8 @@ single library call per step, and no blocking or fusion:
 """
 from __future__ import annotations
 
+import bisect
+
 import numpy as np
 
 
@@ -67,9 +69,10 @@ def join_pairs(probe_keys, sorted_build_keys):
     pr = np.zeros(total, dtype=np.uint64)
     br = np.zeros(total, dtype=np.uint64)
     nonempty = [j for j in range(len(cnt)) if cnt[j] > 0]
+    starts = [int(off[j]) for j in nonempty]
     for n in range(total):
-        # the one non-empty range holding position n
-        j = max(jj for jj in nonempty if off[jj] <= n)
+        # the one non-empty range holding position n: the last start <= n
+        j = nonempty[bisect.bisect_right(starts, n) - 1]
         start = idx[int(probe[j])][0]
         pr[n] = j
         br[n] = start + (n - int(off[j]))

@@ -1,0 +1,505 @@
+"""Python binding of libcdl (include/cdl.h): argument marshalling only.
+
+Every step of the fixpoint runs in the library's sm_103a kernels.  PyTorch
+supplies device memory (through the engine's allocator callbacks, or as the
+tensors handed to the single-step calls) and the CUDA stream.  There is no
+CPU fallback: if libcdl.so is missing or no GPU is visible, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcdl.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "cdl.h")
+
+MAX_ARITY = 4
+STATUS = {0: "CDL_OK", -1: "CDL_E_INVALID", -2: "CDL_E_NOMEM", -3: "CDL_E_CAPACITY",
+          -4: "CDL_E_VALUE", -5: "CDL_E_MAXITER", -6: "CDL_E_TIMEOUT", -7: "CDL_E_CUDA",
+          -8: "CDL_E_STATE"}
+
+
+class CdlError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{self.name}: {msg}" if msg else self.name)
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p), ("mem_limit", ctypes.c_uint64),
+                ("max_iters", ctypes.c_uint64), ("spin_limit", ctypes.c_uint64),
+                ("timing", ctypes.c_uint32), ("estimator", ctypes.c_int32),
+                ("hash_load", ctypes.c_double), ("radix_bits", ctypes.c_uint32),
+                ("log_path", ctypes.c_char_p)]
+
+
+class Term(ctypes.Structure):
+    _fields_ = [("is_const", ctypes.c_uint32), ("v", ctypes.c_uint32)]
+
+
+class Atom(ctypes.Structure):
+    _fields_ = [("rel", ctypes.c_uint32), ("arity", ctypes.c_uint32),
+                ("terms", ctypes.POINTER(Term))]
+
+
+class RuleS(ctypes.Structure):
+    _fields_ = [("head", Atom), ("nbody", ctypes.c_uint32), ("body", ctypes.POINTER(Atom)),
+                ("nneq", ctypes.c_uint32), ("neq", ctypes.POINTER(ctypes.c_uint32))]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_uint64), ("rounds", ctypes.c_uint64),
+                ("derived_tuples", ctypes.c_uint64), ("seconds", ctypes.c_double),
+                ("algo_bytes", ctypes.c_double), ("joins", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64), ("est_predictions", ctypes.c_uint64),
+                ("est_overflows", ctypes.c_uint64),
+                ("delta_per_round", ctypes.POINTER(ctypes.c_uint64)),
+                ("delta_cap", ctypes.c_uint64)]
+
+
+class ColRef(ctypes.Structure):
+    _fields_ = [("side", ctypes.c_uint32), ("v", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def header_functions() -> list:
+    """Names of the functions include/cdl.h declares."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(cdl_\w+)\s*\(", src, flags=re.M)))
+
+
+def lib():
+    """Loads libcdl.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() or "
+                           "python -m paper_2501_13051_gb300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    P, U64, U32, VP = ctypes.POINTER, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
+    PP = P(ctypes.c_void_p)
+    sig = {
+        "cdl_options_default": (None, [P(Options)]),
+        "cdl_create": (ctypes.c_int, [P(Options), P(VP)]),
+        "cdl_destroy": (ctypes.c_int, [VP]),
+        "cdl_relation_create": (ctypes.c_int, [VP, ctypes.c_char_p, U32, P(U32)]),
+        "cdl_relation_load": (ctypes.c_int, [VP, U32, PP, U64, ctypes.c_int]),
+        "cdl_rule_add": (ctypes.c_int, [VP, P(RuleS)]),
+        "cdl_run": (ctypes.c_int, [VP, P(Stats)]),
+        "cdl_relation_size": (ctypes.c_int, [VP, U32, P(U64)]),
+        "cdl_relation_export": (ctypes.c_int, [VP, U32, PP, U64, P(U64), ctypes.c_int]),
+        "cdl_kernel_profile": (ctypes.c_int, [VP, U32, ctypes.c_char_p, ctypes.c_size_t, P(U64),
+                                              P(ctypes.c_double), P(ctypes.c_double)]),
+        "cdl_last_error": (ctypes.c_char_p, [VP]),
+        "cdl_hash_table_bytes": (U64, [U64, ctypes.c_double]),
+        "cdl_hash_build": (ctypes.c_int, [VP, U64, VP, U64, VP]),
+        "cdl_join_count": (ctypes.c_int, [VP, U64, VP, U64, VP, VP]),
+        "cdl_exclusive_scan": (ctypes.c_int, [VP, U64, VP, P(U64), VP, P(ctypes.c_size_t), VP]),
+        "cdl_join": (ctypes.c_int, [PP, U32, U64, U32, PP, U32, U64, U32, P(ColRef), U32,
+                                    P(ColRef), U32, PP, U64, P(U64), VP, P(ctypes.c_size_t), VP]),
+        "cdl_sort_unique": (ctypes.c_int, [PP, U32, U64, PP, P(U64), VP, P(ctypes.c_size_t), VP]),
+        "cdl_diff_merge": (ctypes.c_int, [PP, U64, PP, U64, U32, PP, P(U64), PP, VP,
+                                          P(ctypes.c_size_t), VP]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return _lib
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libcdl needs a CUDA GPU; none is visible")
+    return torch
+
+
+def _ptrs(tensors) -> ctypes.Array:
+    arr = (ctypes.c_void_p * max(1, len(tensors)))()
+    for i, t in enumerate(tensors):
+        arr[i] = t.data_ptr() if hasattr(t, "data_ptr") else t
+    return arr
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class _TorchArena:
+    """Allocator callbacks that hand the engine torch-owned device memory."""
+
+    def __init__(self, device):
+        self.torch = _torch()
+        self.device = device
+        self.live = {}
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, _ctx):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except Exception:  # out of memory -> NULL, the engine reports CDL_E_NOMEM
+            return None
+        self.live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(self, ptr, _nbytes, _ctx):
+        self.live.pop(ptr, None)
+
+
+@dataclass
+class RunStats:
+    iterations: int
+    rounds: int
+    derived_tuples: int
+    seconds: float
+    algo_bytes: float
+    joins: int
+    kernel_launches: int
+    delta_per_round: list = field(default_factory=list)
+
+
+class Engine:
+    """One engine on the current CUDA device and stream (cdl_create)."""
+
+    def __init__(self, *, device=None, stream=None, mem_limit=0, max_iters=0, spin_limit=0,
+                 timing=False, hash_load=0.5, radix_bits=8, torch_alloc=True):
+        torch = _torch()
+        L = lib()
+        self._L = L
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        opts = Options()
+        L.cdl_options_default(ctypes.byref(opts))
+        self._arena = _TorchArena(self.device) if torch_alloc else None
+        if self._arena is not None:
+            opts.alloc = self._arena.alloc_cb
+            opts.free = self._arena.free_cb
+        opts.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        opts.mem_limit = mem_limit
+        opts.max_iters = max_iters
+        opts.spin_limit = spin_limit
+        opts.timing = 1 if timing else 0
+        opts.hash_load = hash_load
+        opts.radix_bits = radix_bits
+        self._opts = opts
+        h = ctypes.c_void_p()
+        self._check(L.cdl_create(ctypes.byref(opts), ctypes.byref(h)), engine=False)
+        self._h = h
+        self.rels = {}
+        self.arity = {}
+
+    def _check(self, st, engine=True):
+        if st != 0:
+            msg = ""
+            if engine and getattr(self, "_h", None):
+                msg = (self._L.cdl_last_error(self._h) or b"").decode()
+            raise CdlError(st, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.cdl_destroy(self._h)
+            self._h = None
+        if self._arena is not None:
+            self._arena.live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ program
+    def relation(self, name: str, arity: int) -> int:
+        out = ctypes.c_uint32()
+        self._check(self._L.cdl_relation_create(self._h, name.encode(), arity, ctypes.byref(out)))
+        self.rels[name] = out.value
+        self.arity[name] = arity
+        return out.value
+
+    def load(self, name: str, rows) -> None:
+        """rows: (n, arity) host array of uint32, or a list of `arity` int32 /
+        uint32 column tensors (CUDA tensors are read on the device, CPU
+        tensors -- e.g. pinned -- are copied from host memory)."""
+        rel, ar = self.rels[name], self.arity[name]
+        if isinstance(rows, (list, tuple)):
+            cols = list(rows)
+            n = cols[0].numel() if cols else 0
+            keep = cols
+            on_dev = 1 if (cols and cols[0].is_cuda) else 0
+        else:
+            a = np.ascontiguousarray(np.asarray(rows, dtype=np.uint32).reshape(-1, ar))
+            n = a.shape[0]
+            keep = [np.ascontiguousarray(a[:, k]) for k in range(ar)]
+            cols = [c.ctypes.data for c in keep]
+            on_dev = 0
+        arr = _ptrs(cols)
+        self._check(self._L.cdl_relation_load(self._h, rel, arr, n, on_dev))
+        del keep
+
+    def rule(self, head, body, neq=()) -> None:
+        var_id = {}
+
+        def atom(a):
+            name, terms = a
+            ts = (Term * len(terms))()
+            for i, t in enumerate(terms):
+                if isinstance(t, str):
+                    ts[i] = Term(0, var_id.setdefault(t, len(var_id)))
+                else:
+                    ts[i] = Term(1, int(t))
+            return Atom(self.rels[name], len(terms), ts), ts
+
+        body_atoms = (Atom * len(body))()
+        keep = []
+        for i, a in enumerate(body):
+            at, ts = atom(a)
+            body_atoms[i] = at
+            keep.append(ts)
+        h, hts = atom(head)
+        nq = (ctypes.c_uint32 * max(1, 2 * len(neq)))()
+        for i, (a, b) in enumerate(neq):
+            nq[2 * i], nq[2 * i + 1] = var_id[a], var_id[b]
+        r = RuleS(h, len(body), body_atoms, len(neq), nq)
+        self._check(self._L.cdl_rule_add(self._h, ctypes.byref(r)))
+
+    def load_program(self, program) -> None:
+        for name, ar in program.arity.items():
+            self.relation(name, ar)
+        for name, rows in program.edb.items():
+            self.load(name, rows)
+        for r in program.rules:
+            self.rule(r.head, r.body, r.neq)
+
+    # ---------------------------------------------------------------- run
+    def run(self) -> RunStats:
+        cap = 1 << 16
+        buf = (ctypes.c_uint64 * cap)()
+        st = Stats()
+        st.delta_per_round = ctypes.cast(buf, ctypes.POINTER(ctypes.c_uint64))
+        st.delta_cap = cap
+        self._check(self._L.cdl_run(self._h, ctypes.byref(st)))
+        return RunStats(st.iterations, st.rounds, st.derived_tuples, st.seconds, st.algo_bytes,
+                        st.joins, st.kernel_launches, [int(buf[i]) for i in range(min(st.rounds, cap))])
+
+    def size(self, name: str) -> int:
+        n = ctypes.c_uint64()
+        self._check(self._L.cdl_relation_size(self._h, self.rels[name], ctypes.byref(n)))
+        return n.value
+
+    def export(self, name: str, device: bool = False, out=None):
+        """Sorted unique tuples: (n, arity) numpy array, or with device=True a
+        list of CUDA int32 column tensors (uint32 bit patterns).  ``out`` may
+        supply host column buffers (e.g. pinned tensors) of sufficient size."""
+        torch = _torch()
+        ar, n = self.arity[name], self.size(name)
+        got = ctypes.c_uint64()
+        if device:
+            cols = [torch.empty(max(n, 1), dtype=torch.int32, device=self.device) for _ in range(ar)]
+            self._check(self._L.cdl_relation_export(self._h, self.rels[name], _ptrs(cols), n,
+                                                    ctypes.byref(got), 1))
+            return [c[:n] for c in cols]
+        if out is not None:
+            self._check(self._L.cdl_relation_export(self._h, self.rels[name], _ptrs(out), n,
+                                                    ctypes.byref(got), 0))
+            return out
+        res = np.zeros((ar, max(n, 1)), dtype=np.uint32)
+        ptrs = _ptrs([res[k].ctypes.data for k in range(ar)])
+        self._check(self._L.cdl_relation_export(self._h, self.rels[name], ptrs, n,
+                                                ctypes.byref(got), 0))
+        return np.ascontiguousarray(res[:, :n].T)
+
+    def kernel_profile(self) -> list:
+        out = []
+        for i in range(64):
+            name = ctypes.create_string_buffer(64)
+            la, ms, by = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
+            st = self._L.cdl_kernel_profile(self._h, i, name, 64, ctypes.byref(la), ctypes.byref(ms),
+                                            ctypes.byref(by))
+            if st != 0:
+                break
+            out.append({"kernel": name.value.decode(), "launches": la.value, "ms": ms.value,
+                        "bytes": by.value})
+        return out
+
+
+def run_program(program, **opts):
+    """Loads and runs a workloads.Program; returns ({name: rows}, RunStats)."""
+    with Engine(**opts) as e:
+        e.load_program(program)
+        st = e.run()
+        return {nm: e.export(nm) for nm in program.arity}, st
+
+
+# ---------------------------------------------------------------------------
+# single steps on torch tensors (device memory owned by the caller)
+# ---------------------------------------------------------------------------
+
+def _u32(t):
+    torch = _torch()
+    if t.dtype not in (torch.int32, torch.uint32) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("columns must be contiguous CUDA int32/uint32 tensors")
+    return t
+
+
+def _workspace(fn, *args):
+    torch = _torch()
+    need = ctypes.c_size_t(0)
+    st = fn(*args, None, ctypes.byref(need))
+    if st != 0:
+        raise CdlError(st)
+    ws = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device="cuda")
+    return ws, need
+
+
+def hash_table_bytes(n_keys: int, load: float = 0.5) -> int:
+    return int(lib().cdl_hash_table_bytes(n_keys, load))
+
+
+def hash_build(keys, load: float = 0.5, stream=None):
+    """Step (a) on a sorted key column; returns the table as a uint8 tensor."""
+    torch = _torch()
+    keys = _u32(keys)
+    nb = hash_table_bytes(keys.numel(), load)
+    table = torch.empty(nb, dtype=torch.uint8, device=keys.device)
+    st = lib().cdl_hash_build(keys.data_ptr(), keys.numel(), table.data_ptr(), nb,
+                              _stream_handle(stream))
+    if st != 0:
+        raise CdlError(st)
+    return table
+
+
+def join_count(probe, table, stream=None):
+    torch = _torch()
+    probe = _u32(probe)
+    counts = torch.empty(max(1, probe.numel()), dtype=torch.int32, device=probe.device)
+    st = lib().cdl_join_count(probe.data_ptr(), probe.numel(), table.data_ptr(), table.numel(),
+                              counts.data_ptr(), _stream_handle(stream))
+    if st != 0:
+        raise CdlError(st)
+    return counts[:probe.numel()]
+
+
+def exclusive_scan(counts, stream=None):
+    torch = _torch()
+    counts = _u32(counts)
+    n = counts.numel()
+    out = torch.empty(max(1, n), dtype=torch.int64, device=counts.device)
+    L, s = lib(), _stream_handle(stream)
+    total = ctypes.c_uint64()
+    need = ctypes.c_size_t(0)
+    st = L.cdl_exclusive_scan(counts.data_ptr(), n, out.data_ptr(), ctypes.byref(total), None,
+                              ctypes.byref(need), s)
+    if st != 0:
+        raise CdlError(st)
+    ws = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device=counts.device)
+    st = L.cdl_exclusive_scan(counts.data_ptr(), n, out.data_ptr(), ctypes.byref(total),
+                              ws.data_ptr(), ctypes.byref(need), s)
+    if st != 0:
+        raise CdlError(st)
+    return out[:n], int(total.value)
+
+
+def join(probe_cols, probe_key, build_cols, build_key, spec, neq=(), out_cap=None, stream=None):
+    """Step (b): the full three-pass join; spec / neq hold (side, v) pairs
+    (side 0 probe column, 1 build column, 2 constant)."""
+    torch = _torch()
+    probe_cols = [_u32(c) for c in probe_cols]
+    build_cols = [_u32(c) for c in build_cols]
+    L, s = lib(), _stream_handle(stream)
+    npr, nbu = probe_cols[0].numel(), build_cols[0].numel()
+    sp = (ColRef * len(spec))(*[ColRef(a, b) for a, b in spec])
+    flat = [x for pair in neq for x in pair]
+    nq = (ColRef * max(1, len(flat)))(*[ColRef(a, b) for a, b in flat])
+    n_out = ctypes.c_uint64()
+    need = ctypes.c_size_t(0)
+    args_head = (_ptrs(probe_cols), len(probe_cols), npr, probe_key, _ptrs(build_cols),
+                 len(build_cols), nbu, build_key, sp, len(spec), nq, len(neq))
+    st = L.cdl_join(*args_head, _ptrs([]), 0, ctypes.byref(n_out), None, ctypes.byref(need), s)
+    if st != 0:
+        raise CdlError(st)
+    ws = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device="cuda")
+    # size query: out_cap 0 reports the unfiltered size
+    outs0 = [torch.empty(1, dtype=torch.int32, device="cuda") for _ in spec]
+    st = L.cdl_join(*args_head, _ptrs(outs0), 0, ctypes.byref(n_out), ws.data_ptr(),
+                    ctypes.byref(need), s)
+    if st not in (0, -3):
+        raise CdlError(st)
+    total = int(n_out.value)
+    cap = total if out_cap is None else out_cap
+    outs = [torch.empty(max(1, cap), dtype=torch.int32, device="cuda") for _ in spec]
+    st = L.cdl_join(*args_head, _ptrs(outs), cap, ctypes.byref(n_out), ws.data_ptr(),
+                    ctypes.byref(need), s)
+    if st != 0:
+        raise CdlError(st)
+    return [o[:n_out.value] for o in outs]
+
+
+def sort_unique(cols, stream=None):
+    """Step (c): sorted unique tuples of the given columns."""
+    torch = _torch()
+    cols = [_u32(c) for c in cols]
+    L, s = lib(), _stream_handle(stream)
+    n = cols[0].numel()
+    outs = [torch.empty(max(1, n), dtype=torch.int32, device="cuda") for _ in cols]
+    n_out = ctypes.c_uint64()
+    need = ctypes.c_size_t(0)
+    st = L.cdl_sort_unique(_ptrs(cols), len(cols), n, _ptrs(outs), ctypes.byref(n_out), None,
+                           ctypes.byref(need), s)
+    if st != 0:
+        raise CdlError(st)
+    ws = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device="cuda")
+    st = L.cdl_sort_unique(_ptrs(cols), len(cols), n, _ptrs(outs), ctypes.byref(n_out),
+                           ws.data_ptr(), ctypes.byref(need), s)
+    if st != 0:
+        raise CdlError(st)
+    return [o[:n_out.value] for o in outs]
+
+
+def diff_merge(full_cols, fresh_cols, stream=None):
+    """Step (d): (delta, merged) for sorted unique full and sorted fresh."""
+    torch = _torch()
+    full_cols = [_u32(c) for c in full_cols]
+    fresh_cols = [_u32(c) for c in fresh_cols]
+    L, s = lib(), _stream_handle(stream)
+    nf, nu, k = full_cols[0].numel(), fresh_cols[0].numel(), len(full_cols)
+    delta = [torch.empty(max(1, nu), dtype=torch.int32, device="cuda") for _ in range(k)]
+    merged = [torch.empty(max(1, nf + nu), dtype=torch.int32, device="cuda") for _ in range(k)]
+    nd = ctypes.c_uint64()
+    need = ctypes.c_size_t(0)
+    args = (_ptrs(full_cols), nf, _ptrs(fresh_cols), nu, k, _ptrs(delta), ctypes.byref(nd),
+            _ptrs(merged))
+    st = L.cdl_diff_merge(*args, None, ctypes.byref(need), s)
+    if st != 0:
+        raise CdlError(st)
+    ws = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device="cuda")
+    st = L.cdl_diff_merge(*args, ws.data_ptr(), ctypes.byref(need), s)
+    if st != 0:
+        raise CdlError(st)
+    d = int(nd.value)
+    return [x[:d] for x in delta], [x[:nf + d] for x in merged]

@@ -1,0 +1,134 @@
+// Shared device helpers of the column-oriented Datalog kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cdl.h"
+
+namespace cdl {
+
+constexpr int kMaxK = CDL_MAX_ARITY;
+constexpr uint32_t kEmpty = CDL_EMPTY_KEY;
+
+// Column sets passed by value to kernels: column k of a relation is c[k].
+struct ColsIn {
+  const uint32_t* c[kMaxK];
+};
+struct ColsOut {
+  uint32_t* c[kMaxK];
+};
+
+// Error bits a kernel may raise in the engine's device status word.
+enum : uint32_t {
+  kErrTimeout = 1u,   // a bounded wait ran out
+  kErrCapacity = 2u,  // an output cursor passed its capacity
+  kErrValue = 4u,     // the reserved value was seen in input
+  kErrTable = 8u      // a hash table had no free slot
+};
+
+// 32-bit finaliser of MurmurHash3 (Austin Appleby, public domain): a
+// bijective mixer, so distinct keys never collide before masking.
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t k) {
+  k ^= k >> 16;
+  k *= 0x85ebca6bu;
+  k ^= k >> 13;
+  k *= 0xc2b2ae35u;
+  k ^= k >> 16;
+  return k;
+}
+
+__host__ __device__ __forceinline__ uint32_t hash_key(uint32_t k0, uint32_t k1) {
+  return mix32(k0 ^ mix32(k1 + 0x9e3779b9u));
+}
+
+// Hash slot of the hybrid index: key (one or two words) -> (start, count) in
+// the build side sorted by key.  An empty slot has k0 == k1 == 0xFFFFFFFF.
+struct __align__(16) Slot {
+  uint32_t k0, k1, start, count;
+};
+
+__device__ __forceinline__ Slot load_slot(const Slot* t, uint64_t i) {
+  const uint4 v = __ldg(reinterpret_cast<const uint4*>(t) + i);
+  return Slot{v.x, v.y, v.z, v.w};
+}
+
+// Linear-probing lookup; returns count (0 if absent) and start.
+__device__ __forceinline__ uint32_t probe_table(const Slot* t, uint64_t mask, uint32_t k0,
+                                                uint32_t k1, uint32_t* start) {
+  uint64_t i = hash_key(k0, k1) & mask;
+  for (uint64_t step = 0; step <= mask; ++step) {
+    const Slot s = load_slot(t, i);
+    if (s.k0 == k0 && s.k1 == k1) {
+      *start = s.start;
+      return s.count;
+    }
+    if (s.k0 == kEmpty && s.k1 == kEmpty) break;
+    i = (i + 1) & mask;
+  }
+  *start = 0;
+  return 0;
+}
+
+// Lexicographic comparison of tuples held in registers.
+template <int K>
+__device__ __forceinline__ bool tuple_le(const uint32_t (&a)[K], const uint32_t (&b)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (a[k] != b[k]) return a[k] < b[k];
+  }
+  return true;
+}
+template <int K>
+__device__ __forceinline__ bool tuple_eq(const uint32_t (&a)[K], const uint32_t (&b)[K]) {
+  bool e = true;
+#pragma unroll
+  for (int k = 0; k < K; ++k) e &= a[k] == b[k];
+  return e;
+}
+template <int K>
+__device__ __forceinline__ void load_tuple(const ColsIn& c, uint64_t i, uint32_t (&t)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) t[k] = c.c[k][i];
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Block-wide exclusive sum over THREADS threads (values per thread), with
+// the block total in *total.  smem: THREADS/32 words.
+template <int THREADS, typename T>
+__device__ __forceinline__ T block_exclusive_sum(T v, T* smem, T* total) {
+  constexpr int W = THREADS / 32;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  T inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T n = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= (uint32_t)o) inc += n;
+  }
+  if (lane == 31) smem[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < (uint32_t)W ? smem[lane] : T(0);
+    T winc = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T n = __shfl_up_sync(0xffffffffu, winc, o);
+      if (lane >= (uint32_t)o) winc += n;
+    }
+    if (lane < (uint32_t)W) smem[lane] = winc - w;
+    if (lane == W - 1) smem[W] = winc;
+  }
+  __syncthreads();
+  const T res = smem[warp] + inc - v;
+  *total = smem[W];
+  __syncthreads();
+  return res;
+}
+
+}  // namespace cdl

@@ -1,0 +1,1205 @@
+// The semi-naive fixpoint engine behind the C ABI (include/cdl.h).
+//
+// Host side of the method: relations as uint32 columns in device memory
+// (Section 3), rules lowered to copy / join / project plans over them
+// (Section 4), and the round loop of semi-naive evaluation with full, delta
+// and new versions, every rule applied once per round and one merge per
+// derived relation per round (Section 3).  Every step of a round runs in the
+// kernels of hash.cu, join.cu, scan.cu, sort.cu and setops.cu; the host only
+// plans, allocates and reads back the sizes it needs to size the next launch.
+//
+// Round r > 1 evaluates, for every rule and every body atom i over a derived
+// relation, the variant that reads delta_{r-1} at atom i and the full
+// relation at every other atom.  (The textbook variant reads full - delta at
+// the atoms before i; reading full instead derives a superset of the same
+// tuples, and the difference with full removes the extra ones, so the
+// delta of every round is unchanged.)  Round 1 applies every rule to the
+// loaded facts.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/cdl.h"
+#include "kernels.h"
+
+using namespace cdl;
+
+namespace {
+
+// ----------------------------------------------------------------- memory
+// Best-fit sub-allocator over chunks obtained from the caller's allocator
+// (or cudaMalloc).  Every kernel of an engine runs on one stream, so a block
+// freed here can be handed to the next launch without a synchronisation.
+class Pool {
+ public:
+  cdl_alloc_fn af = nullptr;
+  cdl_free_fn ff = nullptr;
+  void* ctx = nullptr;
+  uint64_t limit = 0;
+  uint64_t held = 0;
+
+  void* get(size_t bytes) {
+    bytes = bytes ? (bytes + 255) & ~size_t(255) : 256;
+    auto it = by_size_.lower_bound(bytes);
+    if (it == by_size_.end()) {
+      if (!grow(bytes)) return nullptr;
+      it = by_size_.lower_bound(bytes);
+      if (it == by_size_.end()) return nullptr;
+    }
+    char* p = it->second;
+    size_t sz = it->first;
+    by_size_.erase(it);
+    Block b = free_[p];
+    free_.erase(p);
+    if (sz - bytes >= 256) {
+      free_[p + bytes] = Block{sz - bytes, b.chunk};
+      by_size_.emplace(sz - bytes, p + bytes);
+      sz = bytes;
+    }
+    used_[p] = Block{sz, b.chunk};
+    return p;
+  }
+
+  void put(void* vp) {
+    char* p = static_cast<char*>(vp);
+    auto it = used_.find(p);
+    if (it == used_.end()) return;
+    Block b = it->second;
+    used_.erase(it);
+    auto nx = free_.find(p + b.size);
+    if (nx != free_.end() && nx->second.chunk == b.chunk) {
+      erase_size(nx->first, nx->second.size);
+      b.size += nx->second.size;
+      free_.erase(nx);
+    }
+    auto pv = free_.lower_bound(p);
+    if (pv != free_.begin()) {
+      --pv;
+      if (pv->first + pv->second.size == p && pv->second.chunk == b.chunk) {
+        erase_size(pv->first, pv->second.size);
+        pv->second.size += b.size;
+        by_size_.emplace(pv->second.size, pv->first);
+        return;
+      }
+    }
+    free_[p] = b;
+    by_size_.emplace(b.size, p);
+  }
+
+  // Returns every chunk with nothing allocated in it to the allocator.
+  void trim() {
+    for (auto it = chunks_.begin(); it != chunks_.end();) {
+      auto f = free_.find(it->first);
+      if (f != free_.end() && f->second.size == it->second) {
+        erase_size(f->first, f->second.size);
+        free_.erase(f);
+        release(it->first, it->second);
+        held -= it->second;
+        it = chunks_.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+
+  void release_all() {
+    for (auto& c : chunks_) release(c.first, c.second);
+    chunks_.clear();
+    free_.clear();
+    by_size_.clear();
+    used_.clear();
+    held = 0;
+  }
+
+ private:
+  struct Block {
+    size_t size;
+    char* chunk;  // base of the chunk the block lies in
+  };
+  std::map<char*, size_t> chunks_;
+  std::map<char*, Block> free_;
+  std::multimap<size_t, char*> by_size_;
+  std::unordered_map<char*, Block> used_;
+
+  void release(char* p, size_t bytes) {
+    if (ff)
+      ff(p, bytes, ctx);
+    else
+      cudaFree(p);
+  }
+
+  void* acquire(size_t want) {
+    void* p = nullptr;
+    if (af) {
+      p = af(want, ctx);
+    } else if (cudaMalloc(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return p;
+  }
+
+  // A new chunk; chunks with nothing in them are returned first so that a
+  // growing relation reuses the memory of its previous, smaller version.
+  bool grow(size_t bytes) {
+    trim();
+    size_t want = std::max(bytes, size_t(64) << 20);
+    if (limit && held + want > limit) {
+      want = bytes;
+      if (held + want > limit) return false;
+    }
+    void* p = acquire(want);
+    if (!p && want > bytes) {
+      want = bytes;
+      p = acquire(want);
+    }
+    if (!p) return false;
+    char* c = static_cast<char*>(p);
+    chunks_[c] = want;
+    held += want;
+    free_[c] = Block{want, c};
+    by_size_.emplace(want, c);
+    return true;
+  }
+  void erase_size(char* p, size_t sz) {
+    auto r = by_size_.equal_range(sz);
+    for (auto i = r.first; i != r.second; ++i)
+      if (i->second == p) {
+        by_size_.erase(i);
+        return;
+      }
+  }
+};
+
+struct DBuf {
+  Pool* pool = nullptr;
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept { swap(o); }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      reset();
+      swap(o);
+    }
+    return *this;
+  }
+  ~DBuf() { reset(); }
+  void reset() {
+    if (pool && p) pool->put(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void swap(DBuf& o) {
+    std::swap(pool, o.pool);
+    std::swap(p, o.p);
+    std::swap(bytes, o.bytes);
+  }
+};
+
+// A relation version or a temporary table: k device columns of cap rows.
+struct DCols {
+  DBuf buf;
+  uint32_t k = 0;
+  uint64_t n = 0, cap = 0;
+  uint32_t* c[kMaxK] = {nullptr, nullptr, nullptr, nullptr};
+  ColsIn in() const {
+    ColsIn r;
+    for (int i = 0; i < kMaxK; ++i) r.c[i] = c[i];
+    return r;
+  }
+  ColsOut out() const {
+    ColsOut r;
+    for (int i = 0; i < kMaxK; ++i) r.c[i] = c[i];
+    return r;
+  }
+  void clear() {
+    buf.reset();
+    n = cap = 0;
+    for (auto& p : c) p = nullptr;
+  }
+};
+
+size_t col_stride(uint64_t cap) { return ((cap ? cap : 1) * 4 + 255) & ~uint64_t(255); }
+
+uint32_t bits_of(uint64_t v) {
+  uint32_t b = 0;
+  while (v) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
+}
+
+enum Ver { kFull = 0, kDelta = 1 };
+
+struct Relation {
+  std::string name;
+  uint32_t arity = 0;
+  bool idb = false;
+  DCols full, delta, fresh;
+  uint64_t fresh_ub = 0;
+  uint32_t bound[kMaxK] = {0, 0, 0, 0};  // every value of column k is <= bound[k]
+  uint64_t version[2] = {1, 1};
+};
+
+struct Term {
+  bool is_const;
+  uint32_t v;
+};
+struct AtomR {
+  uint32_t rel;
+  std::vector<Term> t;
+};
+struct RuleR {
+  AtomR head;
+  std::vector<AtomR> body;
+  std::vector<std::pair<uint32_t, uint32_t>> neq;
+};
+
+// A hybrid index: the version's tuples sorted by the key columns first and
+// the hash table over the distinct keys.
+struct Index {
+  int rel = -1, ver = -1;
+  uint64_t version = 0;
+  std::vector<uint32_t> key;
+  DCols sorted;  // unused when the relation's own order already starts with the key
+  const uint32_t* cols[kMaxK] = {nullptr, nullptr, nullptr, nullptr};  // original numbering
+  uint64_t n = 0;
+  DBuf table;
+  uint64_t slots = 0;
+};
+
+// A table the join chain reads: columns hold the listed variables.
+struct Src {
+  const uint32_t* c[kMaxK] = {nullptr, nullptr, nullptr, nullptr};
+  uint64_t n = 0;
+  uint32_t k = 0;
+  std::vector<uint32_t> vars;
+  std::vector<uint32_t> bits;
+  int rel = -1, ver = -1;  // a relation version's own columns, else -1
+  DCols owned;
+  ColsIn in() const {
+    ColsIn r;
+    for (int i = 0; i < kMaxK; ++i) r.c[i] = c[i];
+    return r;
+  }
+};
+
+constexpr uint32_t kMaxRels = 1024;
+// control block slots (uint64): 0 error word, 1 scratch, 2 aux cursor,
+// 4 + r fresh cursor of relation r, 4 + kMaxRels + r delta size of r
+constexpr uint32_t kSlotErr = 0, kSlotScratch = 1, kSlotAux = 2, kSlotCursor = 4,
+                   kSlotDelta = 4 + kMaxRels, kCtlSlots = 4 + 2 * kMaxRels;
+
+}  // namespace
+
+struct cdl_engine {
+  cdl_options opt{};
+  cudaStream_t st = nullptr;
+  Pool pool;
+  Profiler prof;
+  Ctx ctx;
+  std::string err;
+  std::vector<std::unique_ptr<Relation>> rels;
+  std::map<std::string, uint32_t> by_name;
+  std::vector<RuleR> rules;
+  bool ran = false;
+  DBuf ctl;
+  uint64_t* h_ctl = nullptr;
+  std::vector<std::unique_ptr<Index>> cache;
+  uint32_t radix_bits = 8;
+  double hash_load = 0.5;
+  uint64_t joins = 0;
+
+  ~cdl_engine() {
+    cache.clear();
+    rels.clear();
+    ctl.reset();
+    pool.release_all();
+    if (h_ctl) cudaFreeHost(h_ctl);
+  }
+
+  cdl_status fail(cdl_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+  cdl_status cuda_fail(cudaError_t e, const char* where) {
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return CDL_E_CUDA;
+  }
+  uint64_t* dslot(uint32_t i) { return static_cast<uint64_t*>(ctl.p) + i; }
+
+  DBuf alloc(size_t bytes) {
+    DBuf b;
+    b.p = pool.get(bytes);
+    if (b.p) {
+      b.pool = &pool;
+      b.bytes = bytes;
+    }
+    return b;
+  }
+  bool alloc_cols(DCols& d, uint32_t k, uint64_t cap) {
+    d.clear();
+    const size_t stride = col_stride(cap);
+    d.buf = alloc(stride * k);
+    if (!d.buf.p) return false;
+    d.k = k;
+    d.cap = cap;
+    for (uint32_t i = 0; i < k; ++i)
+      d.c[i] = reinterpret_cast<uint32_t*>(static_cast<char*>(d.buf.p) + stride * i);
+    return true;
+  }
+
+  // Copies control slots [first, first + count) and the error word to the
+  // host and waits for the stream.
+  cdl_status fetch(uint32_t first, uint32_t count) {
+    cudaError_t e = cudaMemcpyAsync(h_ctl, dslot(kSlotErr), sizeof(uint64_t),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && count)
+      e = cudaMemcpyAsync(h_ctl + first, dslot(first), sizeof(uint64_t) * count,
+                          cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "fetch");
+    const uint32_t flags = (uint32_t)h_ctl[kSlotErr];
+    if (flags & kErrTimeout) return fail(CDL_E_TIMEOUT, "a device-side wait ran out");
+    if (flags & kErrValue) return fail(CDL_E_VALUE, "input holds the reserved value 0xFFFFFFFF");
+    if (flags & kErrCapacity) return fail(CDL_E_CAPACITY, "an output buffer overflowed");
+    if (flags & kErrTable) return fail(CDL_E_CAPACITY, "a hash table ran out of slots");
+    return CDL_OK;
+  }
+
+  // ------------------------------------------------------------- sorting
+  // Sorts d (n rows) lexicographically in place; bits[k] bounds column k.
+  cdl_status sort_cols(DCols& d, const uint32_t* bits) {
+    if (d.n <= 1) return CDL_OK;
+    RadixPlan plan = make_radix_plan(d.k, bits, radix_bits);
+    if (plan.npass == 0) return CDL_OK;
+    DCols alt;
+    if (!alloc_cols(alt, d.k, d.n)) return fail(CDL_E_NOMEM, "sort buffer");
+    DBuf ws = alloc(radix_workspace(d.n, plan.bits));
+    if (!ws.p) return fail(CDL_E_NOMEM, "sort workspace");
+    bool in_b = false;
+    cudaError_t e = radix_sort(ctx, plan, d.out(), alt.out(), d.n, ws.p, &in_b);
+    if (e != cudaSuccess) return cuda_fail(e, "radix_sort");
+    if (in_b) {
+      alt.n = d.n;
+      std::swap(d, alt);
+    }
+    return CDL_OK;
+  }
+
+  // merged = full U fresh (fresh sorted, repeats allowed); delta = fresh - full.
+  cdl_status merge_into(Relation& r, DCols& fresh, DCols* delta_out, uint32_t delta_slot) {
+    DCols merged, delta;
+    if (!alloc_cols(merged, r.arity, r.full.n + fresh.n) || !alloc_cols(delta, r.arity, fresh.n))
+      return fail(CDL_E_NOMEM, "merge buffers");
+    DBuf ws = alloc(diff_merge_workspace(r.full.n, fresh.n));
+    if (!ws.p) return fail(CDL_E_NOMEM, "merge workspace");
+    cudaError_t e = diff_merge(ctx, r.arity, r.full.in(), r.full.n, fresh.in(), fresh.n,
+                               delta.out(), merged.out(), dslot(delta_slot), ws.p);
+    if (e != cudaSuccess) return cuda_fail(e, "diff_merge");
+    merged.n = r.full.n;  // grows by |delta| once it is read back
+    r.full = std::move(merged);
+    r.version[kFull]++;
+    if (delta_out) *delta_out = std::move(delta);
+    return CDL_OK;
+  }
+
+  // ------------------------------------------------------------- indexes
+  cdl_status get_index(const Src& s, const std::vector<uint32_t>& key, Index** out,
+                       std::unique_ptr<Index>& temp) {
+    const bool cacheable = s.rel >= 0;
+    if (cacheable) {
+      const uint64_t v = rels[s.rel]->version[s.ver];
+      for (auto& ix : cache)
+        if (ix->rel == s.rel && ix->ver == s.ver && ix->version == v && ix->key == key) {
+          *out = ix.get();
+          return CDL_OK;
+        }
+    }
+    auto ix = std::make_unique<Index>();
+    ix->rel = s.rel;
+    ix->ver = s.ver;
+    ix->version = cacheable ? rels[s.rel]->version[s.ver] : 0;
+    ix->key = key;
+    ix->n = s.n;
+    bool prefix = true;
+    for (size_t i = 0; i < key.size(); ++i) prefix &= key[i] == i;
+    if (prefix) {
+      for (uint32_t c = 0; c < s.k; ++c) ix->cols[c] = s.c[c];
+    } else {
+      std::vector<uint32_t> perm = key;
+      for (uint32_t c = 0; c < s.k; ++c)
+        if (std::find(key.begin(), key.end(), c) == key.end()) perm.push_back(c);
+      if (!alloc_cols(ix->sorted, s.k, s.n)) return fail(CDL_E_NOMEM, "index copy");
+      ix->sorted.n = s.n;
+      uint32_t pbits[kMaxK];
+      for (uint32_t i = 0; i < s.k; ++i) {
+        cudaError_t e = cudaMemcpyAsync(ix->sorted.c[i], s.c[perm[i]], s.n * 4,
+                                        cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "index copy");
+        pbits[i] = s.bits[perm[i]];
+      }
+      cdl_status r = sort_cols(ix->sorted, pbits);
+      if (r != CDL_OK) return r;
+      for (uint32_t i = 0; i < s.k; ++i) ix->cols[perm[i]] = ix->sorted.c[i];
+    }
+    const uint32_t* k0 = ix->cols[key[0]];
+    const uint32_t* k1 = key.size() > 1 ? ix->cols[key[1]] : nullptr;
+    cudaError_t e = count_heads(ctx, k0, k1, s.n, dslot(kSlotScratch));
+    if (e != cudaSuccess) return cuda_fail(e, "count_heads");
+    cdl_status r = fetch(kSlotScratch, 1);
+    if (r != CDL_OK) return r;
+    ix->slots = table_slots(h_ctl[kSlotScratch], hash_load);
+    ix->table = alloc(ix->slots * sizeof(Slot));
+    if (!ix->table.p) return fail(CDL_E_NOMEM, "hash table");
+    e = hash_build(ctx, k0, k1, s.n, static_cast<Slot*>(ix->table.p), ix->slots);
+    if (e != cudaSuccess) return cuda_fail(e, "hash_build");
+    *out = ix.get();
+    if (cacheable)
+      cache.push_back(std::move(ix));
+    else
+      temp = std::move(ix);
+    return CDL_OK;
+  }
+
+  void evict_stale() {
+    cache.erase(std::remove_if(cache.begin(), cache.end(),
+                               [&](const std::unique_ptr<Index>& ix) {
+                                 return ix->version != rels[ix->rel]->version[ix->ver];
+                               }),
+                cache.end());
+  }
+
+  // --------------------------------------------------------- fresh buffers
+  cdl_status ensure_fresh(Relation& r, uint64_t extra) {
+    const uint64_t need = r.fresh_ub + extra;
+    if (need <= r.fresh.cap && r.fresh.buf.p) {
+      r.fresh_ub = need;
+      return CDL_OK;
+    }
+    DCols nf;
+    uint64_t cap = std::max<uint64_t>(need, r.fresh.cap + r.fresh.cap / 2);
+    if (cap < 1024) cap = 1024;
+    if (!alloc_cols(nf, r.arity, cap)) return fail(CDL_E_NOMEM, "new-tuple buffer");
+    if (r.fresh.buf.p && r.fresh_ub) {
+      for (uint32_t k = 0; k < r.arity; ++k) {
+        cudaError_t e = cudaMemcpyAsync(nf.c[k], r.fresh.c[k], r.fresh_ub * 4,
+                                        cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "grow new-tuple buffer");
+      }
+    }
+    r.fresh = std::move(nf);
+    r.fresh_ub = need;
+    return CDL_OK;
+  }
+
+  // ------------------------------------------------------------- atoms
+  Src rel_src(uint32_t rel, int ver) {
+    Relation& R = *rels[rel];
+    const DCols& d = ver == kDelta ? R.delta : R.full;
+    Src s;
+    for (uint32_t k = 0; k < R.arity; ++k) {
+      s.c[k] = d.c[k];
+      s.bits.push_back(bits_of(R.bound[k]));
+    }
+    s.n = d.n;
+    s.k = R.arity;
+    s.rel = (int)rel;
+    s.ver = ver;
+    return s;
+  }
+
+  // The atom's relation version as a table over its distinct variables,
+  // through a selection when it holds constants or repeated variables.
+  cdl_status atom_src(const AtomR& a, int ver, Src& out) {
+    Src base = rel_src(a.rel, ver);
+    std::vector<uint32_t> vars;
+    bool plain = true;
+    for (const Term& t : a.t) {
+      if (t.is_const || std::find(vars.begin(), vars.end(), t.v) != vars.end())
+        plain = false;
+      else
+        vars.push_back(t.v);
+    }
+    if (plain) {
+      out = std::move(base);
+      out.vars = vars;
+      return CDL_OK;
+    }
+    SelectSpec sp{};
+    sp.in = base.in();
+    sp.in_k = base.k;
+    sp.n = base.n;
+    std::vector<uint32_t> first_col;
+    std::vector<uint32_t> seen;
+    for (uint32_t k = 0; k < a.t.size(); ++k) {
+      const Term& t = a.t[k];
+      if (t.is_const) {
+        sp.const_col[sp.n_const] = k;
+        sp.const_val[sp.n_const++] = t.v;
+      } else {
+        auto it = std::find(seen.begin(), seen.end(), t.v);
+        if (it != seen.end()) {
+          sp.same[sp.n_same][0] = first_col[it - seen.begin()];
+          sp.same[sp.n_same++][1] = k;
+        } else {
+          seen.push_back(t.v);
+          first_col.push_back(k);
+        }
+      }
+    }
+    sp.out_k = (uint32_t)seen.size();
+    for (uint32_t i = 0; i < sp.out_k; ++i) sp.out[i] = Ref{0, first_col[i]};
+    out = Src();
+    out.vars = seen;
+    out.k = sp.out_k;
+    if (sp.out_k == 0) {  // an atom without variables only tests for a matching tuple
+      sp.out_k = 1;
+      sp.out[0] = Ref{0, 0};
+    }
+    if (!alloc_cols(out.owned, sp.out_k, base.n)) return fail(CDL_E_NOMEM, "selection buffer");
+    for (uint32_t i = 0; i < out.k; ++i) {
+      out.c[i] = out.owned.c[i];
+      out.bits.push_back(base.bits[first_col[i]]);
+    }
+    cudaError_t e = cudaMemsetAsync(dslot(kSlotAux), 0, 8, st);
+    if (e == cudaSuccess) e = select_project(ctx, sp, out.owned.out(), dslot(kSlotAux), base.n);
+    if (e != cudaSuccess) return cuda_fail(e, "select");
+    cdl_status r = fetch(kSlotAux, 1);
+    if (r != CDL_OK) return r;
+    out.n = out.owned.n = h_ctl[kSlotAux];
+    return CDL_OK;
+  }
+
+  // --------------------------------------------------------------- rules
+  cdl_status eval_copy(const RuleR& rule, int ver) {
+    const AtomR& a = rule.body[0];
+    Src base = rel_src(a.rel, ver);
+    if (base.n == 0) return CDL_OK;
+    SelectSpec sp{};
+    sp.in = base.in();
+    sp.in_k = base.k;
+    sp.n = base.n;
+    std::map<uint32_t, uint32_t> col_of;
+    for (uint32_t k = 0; k < a.t.size(); ++k) {
+      const Term& t = a.t[k];
+      if (t.is_const) {
+        sp.const_col[sp.n_const] = k;
+        sp.const_val[sp.n_const++] = t.v;
+      } else if (col_of.count(t.v)) {
+        sp.same[sp.n_same][0] = col_of[t.v];
+        sp.same[sp.n_same++][1] = k;
+      } else {
+        col_of[t.v] = k;
+      }
+    }
+    sp.out_k = (uint32_t)rule.head.t.size();
+    for (uint32_t k = 0; k < sp.out_k; ++k) {
+      const Term& t = rule.head.t[k];
+      sp.out[k] = t.is_const ? Ref{2, t.v} : Ref{0, col_of.at(t.v)};
+    }
+    for (auto& ne : rule.neq) {
+      sp.neq[sp.n_neq][0] = Ref{0, col_of.at(ne.first)};
+      sp.neq[sp.n_neq++][1] = Ref{0, col_of.at(ne.second)};
+    }
+    Relation& H = *rels[rule.head.rel];
+    cdl_status r = ensure_fresh(H, base.n);
+    if (r != CDL_OK) return r;
+    cudaError_t e = select_project(ctx, sp, H.fresh.out(), dslot(kSlotCursor + rule.head.rel),
+                                   H.fresh.cap);
+    return e == cudaSuccess ? CDL_OK : cuda_fail(e, "copy rule");
+  }
+
+  // One variant of a rule with >= 2 body atoms: a left-deep chain of
+  // hash joins starting at atom `start` (the delta atom of the variant).
+  // Writes the head tuples of a rule whose join chain is a single table
+  // (s) or empty (s == null: a body of variable-free atoms, all matched).
+  cdl_status emit_from(const RuleR& rule, const Src* s, const Src& any) {
+    SelectSpec sp{};
+    if (s) {
+      sp.in = s->in();
+      sp.in_k = s->k;
+      sp.n = s->n;
+    } else {
+      sp.in.c[0] = any.owned.c[0];
+      sp.in_k = 1;
+      sp.n = 1;
+    }
+    auto col = [&](uint32_t v) {
+      return (uint32_t)(std::find(s->vars.begin(), s->vars.end(), v) - s->vars.begin());
+    };
+    sp.out_k = (uint32_t)rule.head.t.size();
+    for (uint32_t k = 0; k < sp.out_k; ++k) {
+      const Term& t = rule.head.t[k];
+      sp.out[k] = t.is_const ? Ref{2, t.v} : Ref{0, col(t.v)};
+    }
+    for (auto& ne : rule.neq) {
+      sp.neq[sp.n_neq][0] = Ref{0, col(ne.first)};
+      sp.neq[sp.n_neq++][1] = Ref{0, col(ne.second)};
+    }
+    Relation& H = *rels[rule.head.rel];
+    cdl_status r = ensure_fresh(H, sp.n);
+    if (r != CDL_OK) return r;
+    cudaError_t e = select_project(ctx, sp, H.fresh.out(), dslot(kSlotCursor + rule.head.rel),
+                                   H.fresh.cap);
+    return e == cudaSuccess ? CDL_OK : cuda_fail(e, "project");
+  }
+
+  // One variant of a rule with >= 2 body atoms: a left-deep chain of
+  // hash joins starting at atom `start` (the delta atom of the variant).
+  // Variable-free atoms only gate the rule; atoms that share no variable
+  // with the chain so far join as a cross product.
+  cdl_status eval_join(const RuleR& rule, const std::vector<int>& vers, size_t start) {
+    const size_t nb_all = rule.body.size();
+    std::vector<Src> atoms(nb_all);
+    std::vector<size_t> chain;
+    for (size_t i = 0; i < nb_all; ++i) {
+      cdl_status r = atom_src(rule.body[i], vers[i], atoms[i]);
+      if (r != CDL_OK) return r;
+      if (atoms[i].n == 0) return CDL_OK;  // joins with an empty table derive nothing
+      if (!atoms[i].vars.empty()) chain.push_back(i);
+    }
+    if (chain.size() <= 1) return emit_from(rule, chain.empty() ? nullptr : &atoms[chain[0]], atoms[0]);
+    if (std::find(chain.begin(), chain.end(), start) == chain.end()) start = chain[0];
+    const size_t nb = chain.size();
+    std::vector<size_t> order{start};
+    std::vector<uint32_t> bound = atoms[start].vars;
+    std::vector<bool> used(nb_all, true);
+    for (size_t i : chain) used[i] = false;
+    used[start] = true;
+    for (size_t t = 1; t < nb; ++t) {
+      size_t pick = nb_all;
+      for (size_t i : chain) {
+        if (used[i]) continue;
+        for (uint32_t v : atoms[i].vars)
+          if (std::find(bound.begin(), bound.end(), v) != bound.end()) {
+            pick = i;
+            break;
+          }
+        if (pick != nb_all) break;
+      }
+      if (pick == nb_all)  // nothing shares a variable: cross product with the next atom
+        for (size_t i : chain)
+          if (!used[i]) {
+            pick = i;
+            break;
+          }
+      used[pick] = true;
+      order.push_back(pick);
+      for (uint32_t v : atoms[pick].vars)
+        if (std::find(bound.begin(), bound.end(), v) == bound.end()) bound.push_back(v);
+    }
+    std::vector<bool> neq_done(rule.neq.size(), false);
+    Src left = std::move(atoms[start]);
+    for (size_t t = 1; t < nb; ++t) {
+      Src& right = atoms[order[t]];
+      const bool last = t + 1 == nb;
+      // roles: the first join may build on either atom; later joins build on the atom
+      bool build_right = true;
+      if (t == 1) {
+        const bool right_static = right.rel >= 0 && !rels[right.rel]->idb;
+        const bool left_static = left.rel >= 0 && !rels[left.rel]->idb;
+        if (!right_static && (left_static || left.n < right.n)) build_right = false;
+      }
+      Src& P = build_right ? left : right;
+      Src& B = build_right ? right : left;
+      std::vector<uint32_t> pkey, bkey;
+      for (uint32_t bc = 0; bc < B.vars.size(); ++bc) {
+        auto it = std::find(P.vars.begin(), P.vars.end(), B.vars[bc]);
+        if (it != P.vars.end()) {
+          bkey.push_back(bc);
+          pkey.push_back((uint32_t)(it - P.vars.begin()));
+        }
+      }
+      auto ref_of = [&](uint32_t v) -> Ref {
+        auto it = std::find(P.vars.begin(), P.vars.end(), v);
+        if (it != P.vars.end()) return Ref{0, (uint32_t)(it - P.vars.begin())};
+        it = std::find(B.vars.begin(), B.vars.end(), v);
+        return Ref{1, (uint32_t)(it - B.vars.begin())};
+      };
+      auto avail = [&](uint32_t v) {
+        return std::find(P.vars.begin(), P.vars.end(), v) != P.vars.end() ||
+               std::find(B.vars.begin(), B.vars.end(), v) != B.vars.end();
+      };
+      std::vector<uint32_t> hkey(bkey.begin(), bkey.begin() + std::min<size_t>(2, bkey.size()));
+      JoinSpec js{};
+      js.probe = P.in();
+      js.n_probe = P.n;
+      std::unique_ptr<Index> temp_ix;
+      cdl_status r = CDL_OK;
+      if (hkey.empty()) {
+        if (B.n > 0xFFFFFFFFull) return fail(CDL_E_CAPACITY, "cross product side too large");
+        js.cross = 1;
+        js.n_build = (uint32_t)B.n;
+        js.pk0 = 0;
+        js.pk1 = 0xFFu;
+        for (uint32_t c = 0; c < B.k; ++c) js.build.c[c] = B.c[c];
+        js.slots = 1;
+      } else {
+        Index* ix = nullptr;
+        r = get_index(B, hkey, &ix, temp_ix);
+        if (r != CDL_OK) return r;
+        js.pk0 = pkey[0];
+        js.pk1 = pkey.size() > 1 ? pkey[1] : 0xFFu;
+        for (uint32_t c = 0; c < B.k; ++c) js.build.c[c] = ix->cols[c];
+        js.table = static_cast<const Slot*>(ix->table.p);
+        js.slots = ix->slots;
+      }
+      for (size_t q = 2; q < bkey.size(); ++q) {
+        if (js.n_eq >= 4) return fail(CDL_E_INVALID, "too many shared variables");
+        js.eq[js.n_eq][0] = Ref{0, pkey[q]};
+        js.eq[js.n_eq++][1] = Ref{1, bkey[q]};
+      }
+      for (size_t q = 0; q < rule.neq.size(); ++q) {
+        if (neq_done[q] || !avail(rule.neq[q].first) || !avail(rule.neq[q].second)) continue;
+        if (js.n_neq >= 4) return fail(CDL_E_INVALID, "too many inequalities");
+        js.neq[js.n_neq][0] = ref_of(rule.neq[q].first);
+        js.neq[js.n_neq++][1] = ref_of(rule.neq[q].second);
+        neq_done[q] = true;
+      }
+      Src next;
+      if (last) {
+        js.out_k = (uint32_t)rule.head.t.size();
+        for (uint32_t k = 0; k < js.out_k; ++k) {
+          const Term& tm = rule.head.t[k];
+          js.out[k] = tm.is_const ? Ref{2, tm.v} : ref_of(tm.v);
+        }
+      } else {
+        std::vector<uint32_t> need;
+        for (const Term& tm : rule.head.t)
+          if (!tm.is_const) need.push_back(tm.v);
+        for (size_t q = 0; q < rule.neq.size(); ++q)
+          if (!neq_done[q]) {
+            need.push_back(rule.neq[q].first);
+            need.push_back(rule.neq[q].second);
+          }
+        for (size_t u = t + 1; u < nb; ++u)
+          for (uint32_t v : atoms[order[u]].vars) need.push_back(v);
+        for (const std::vector<uint32_t>* vs : {&P.vars, &B.vars})
+          for (uint32_t v : *vs)
+            if (std::find(need.begin(), need.end(), v) != need.end() &&
+                std::find(next.vars.begin(), next.vars.end(), v) == next.vars.end())
+              next.vars.push_back(v);
+        if (next.vars.size() > (size_t)kMaxK) return fail(CDL_E_INVALID, "intermediate too wide");
+        js.out_k = (uint32_t)next.vars.size();
+        for (uint32_t k = 0; k < js.out_k; ++k) {
+          js.out[k] = ref_of(next.vars[k]);
+          const Src& from = js.out[k].side == 0 ? P : B;
+          next.bits.push_back(from.bits[js.out[k].v]);
+        }
+      }
+      // passes 1 and 2: counts, offsets, total
+      DBuf off = alloc(std::max<uint64_t>(P.n, 1) * 8);
+      DBuf ws = alloc(join_count_workspace(P.n));
+      if (!off.p || !ws.p) return fail(CDL_E_NOMEM, "join offsets");
+      cudaError_t e = join_count_scan(ctx, js, static_cast<uint64_t*>(off.p), dslot(kSlotScratch),
+                                      ws.p);
+      if (e != cudaSuccess) return cuda_fail(e, "join count");
+      r = fetch(kSlotScratch, kSlotCursor + (uint32_t)rels.size() - kSlotScratch);
+      if (r != CDL_OK) return r;
+      const uint64_t total = h_ctl[kSlotScratch];
+      ++joins;
+      if (total == 0) return CDL_OK;
+      const bool filter = js.n_neq > 0 || js.n_eq > 0;
+      if (last) {
+        Relation& H = *rels[rule.head.rel];
+        H.fresh_ub = h_ctl[kSlotCursor + rule.head.rel];
+        const uint64_t base = H.fresh_ub;
+        r = ensure_fresh(H, total);
+        if (r != CDL_OK) return r;
+        e = join_write(ctx, js, static_cast<const uint64_t*>(off.p), total, H.fresh.out(), base,
+                       dslot(kSlotCursor + rule.head.rel), H.fresh.cap);
+        if (e != cudaSuccess) return cuda_fail(e, "join write");
+        return CDL_OK;
+      }
+      next.k = js.out_k;
+      if (!alloc_cols(next.owned, next.k, total)) return fail(CDL_E_NOMEM, "join intermediate");
+      for (uint32_t k = 0; k < next.k; ++k) next.c[k] = next.owned.c[k];
+      e = cudaMemsetAsync(dslot(kSlotAux), 0, 8, st);
+      if (e == cudaSuccess)
+        e = join_write(ctx, js, static_cast<const uint64_t*>(off.p), total, next.owned.out(), 0,
+                       dslot(kSlotAux), total);
+      if (e != cudaSuccess) return cuda_fail(e, "join write");
+      if (filter) {
+        r = fetch(kSlotAux, 1);
+        if (r != CDL_OK) return r;
+        next.n = h_ctl[kSlotAux];
+      } else {
+        next.n = total;
+      }
+      next.owned.n = next.n;
+      if (next.n == 0) return CDL_OK;
+      left = std::move(next);
+    }
+    return CDL_OK;
+  }
+
+  cdl_status eval_rule(const RuleR& rule, bool first_round) {
+    const size_t nb = rule.body.size();
+    if (first_round) {
+      if (nb == 1) return eval_copy(rule, kFull);
+      return eval_join(rule, std::vector<int>(nb, kFull), 0);
+    }
+    for (size_t i = 0; i < nb; ++i) {
+      const Relation& R = *rels[rule.body[i].rel];
+      if (!R.idb || R.delta.n == 0) continue;
+      std::vector<int> vers(nb, kFull);
+      vers[i] = kDelta;
+      cdl_status r = nb == 1 ? eval_copy(rule, kDelta) : eval_join(rule, vers, i);
+      if (r != CDL_OK) return r;
+    }
+    return CDL_OK;
+  }
+
+  // Upper bounds of every column's values: loaded maxima and rule constants,
+  // propagated through the rules to a fixpoint.
+  void propagate_bounds() {
+    bool changed = true;
+    while (changed) {
+      changed = false;
+      for (const RuleR& rule : rules) {
+        std::map<uint32_t, uint32_t> vb;
+        for (const AtomR& a : rule.body)
+          for (uint32_t k = 0; k < a.t.size(); ++k)
+            if (!a.t[k].is_const) {
+              const uint32_t b = rels[a.rel]->bound[k];
+              auto it = vb.find(a.t[k].v);
+              if (it == vb.end())
+                vb[a.t[k].v] = b;
+              else
+                it->second = std::min(it->second, b);
+            }
+        Relation& H = *rels[rule.head.rel];
+        for (uint32_t k = 0; k < rule.head.t.size(); ++k) {
+          const Term& tm = rule.head.t[k];
+          const uint32_t b = tm.is_const ? tm.v : vb[tm.v];
+          if (b > H.bound[k]) {
+            H.bound[k] = b;
+            changed = true;
+          }
+        }
+      }
+    }
+  }
+
+  cdl_status run(cdl_stats* stats) {
+    if (ran) return fail(CDL_E_STATE, "cdl_run was already called");
+    ran = true;
+    for (auto& r : rels) r->idb = false;
+    for (const RuleR& rule : rules) rels[rule.head.rel]->idb = true;
+    propagate_bounds();
+    prof.reset();
+    joins = 0;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    cudaEventRecord(t0, st);
+    uint64_t iterations = 0, rounds = 0;
+    std::vector<uint64_t> per_round;
+    cdl_status status = CDL_OK;
+    const uint32_t nr = (uint32_t)rels.size();
+    for (uint64_t round = 1; status == CDL_OK; ++round) {
+      cudaError_t e = cudaMemsetAsync(dslot(kSlotCursor), 0, 8 * nr, st);
+      if (e != cudaSuccess) {
+        status = cuda_fail(e, "round reset");
+        break;
+      }
+      for (auto& r : rels) r->fresh_ub = 0;
+      for (const RuleR& rule : rules) {
+        status = eval_rule(rule, round == 1);
+        if (status != CDL_OK) break;
+      }
+      if (status != CDL_OK) break;
+      status = fetch(kSlotCursor, nr);
+      if (status != CDL_OK) break;
+      for (uint32_t i = 0; i < nr; ++i) {
+        Relation& R = *rels[i];
+        if (!R.idb) continue;
+        R.fresh.n = h_ctl[kSlotCursor + i];
+        R.delta.clear();
+        R.delta.k = R.arity;
+        R.version[kDelta]++;
+        e = cudaMemsetAsync(dslot(kSlotDelta + i), 0, 8, st);
+        if (e != cudaSuccess) {
+          status = cuda_fail(e, "delta reset");
+          break;
+        }
+        if (R.fresh.n == 0) continue;
+        if (R.full.n + R.fresh.n > 0xFFFFFFFFull) {
+          status = fail(CDL_E_CAPACITY, "relation " + R.name + " would exceed 2^32 tuples");
+          break;
+        }
+        uint32_t bits[kMaxK];
+        for (uint32_t k = 0; k < R.arity; ++k) bits[k] = bits_of(R.bound[k]);
+        status = sort_cols(R.fresh, bits);
+        if (status != CDL_OK) break;
+        status = merge_into(R, R.fresh, &R.delta, kSlotDelta + i);
+        if (status != CDL_OK) break;
+      }
+      if (status != CDL_OK) break;
+      status = fetch(kSlotDelta, nr);
+      if (status != CDL_OK) break;
+      uint64_t new_total = 0;
+      for (uint32_t i = 0; i < nr; ++i) {
+        Relation& R = *rels[i];
+        if (!R.idb) continue;
+        const uint64_t nd = R.fresh.n ? h_ctl[kSlotDelta + i] : 0;
+        R.delta.n = nd;
+        R.full.n += nd;
+        if (R.fresh.n) prof.add_bytes(kDiffMerge, 8.0 * R.arity * nd);
+        new_total += nd;
+      }
+      evict_stale();
+      rounds = round;
+      per_round.push_back(new_total);
+      if (new_total == 0) break;
+      iterations = round;
+      if (opt.max_iters && iterations > opt.max_iters) {
+        status = fail(CDL_E_MAXITER, "the fixpoint needs more rounds than max_iters");
+        break;
+      }
+    }
+    cudaEventRecord(t1, st);
+    cudaEventSynchronize(t1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    prof.collect();
+    for (auto& r : rels) {
+      r->fresh.clear();
+      r->fresh_ub = 0;
+    }
+    if (stats) {
+      stats->iterations = iterations;
+      stats->rounds = rounds;
+      uint64_t derived = 0;
+      for (auto& r : rels)
+        if (r->idb) derived += r->full.n;
+      stats->derived_tuples = derived;
+      stats->seconds = ms * 1e-3;
+      stats->algo_bytes = prof.total_bytes;
+      stats->joins = joins;
+      stats->kernel_launches = prof.total_launches;
+      stats->est_predictions = 0;
+      stats->est_overflows = 0;
+      if (stats->delta_per_round)
+        for (uint64_t i = 0; i < per_round.size() && i < stats->delta_cap; ++i)
+          stats->delta_per_round[i] = per_round[i];
+    }
+    return status;
+  }
+
+  cdl_status load(uint32_t rel, const uint32_t* const* cols, uint64_t n, int on_device) {
+    if (ran) return fail(CDL_E_STATE, "loads must precede cdl_run");
+    Relation& R = *rels[rel];
+    if (n == 0) return CDL_OK;
+    if (n > 0xFFFFFFFFull) return fail(CDL_E_CAPACITY, "load exceeds 2^32 tuples");
+    DCols in;
+    if (!alloc_cols(in, R.arity, n)) return fail(CDL_E_NOMEM, "load buffer");
+    in.n = n;
+    for (uint32_t k = 0; k < R.arity; ++k) {
+      if (!cols[k]) return fail(CDL_E_INVALID, "null column pointer");
+      cudaError_t e = cudaMemcpyAsync(in.c[k], cols[k], n * 4,
+                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                      st);
+      if (e != cudaSuccess) return cuda_fail(e, "load copy");
+    }
+    uint32_t* dmax = reinterpret_cast<uint32_t*>(dslot(kSlotScratch + 1));  // slots 2..3
+    cudaError_t e = check_values(ctx, in.in(), R.arity, n, dmax);
+    if (e != cudaSuccess) return cuda_fail(e, "load check");
+    cdl_status r = fetch(kSlotScratch + 1, 2);
+    if (r != CDL_OK) {
+      cudaMemsetAsync(dslot(kSlotErr), 0, 8, st);
+      return r;
+    }
+    const uint32_t* hmax = reinterpret_cast<const uint32_t*>(h_ctl + kSlotScratch + 1);
+    uint32_t bits[kMaxK];
+    for (uint32_t k = 0; k < R.arity; ++k) {
+      R.bound[k] = std::max(R.bound[k], hmax[k]);
+      bits[k] = bits_of(hmax[k]);
+    }
+    r = sort_cols(in, bits);
+    if (r != CDL_OK) return r;
+    r = merge_into(R, in, nullptr, kSlotScratch);
+    if (r != CDL_OK) return r;
+    r = fetch(kSlotScratch, 1);
+    if (r != CDL_OK) return r;
+    R.full.n += h_ctl[kSlotScratch];
+    evict_stale();
+    return CDL_OK;
+  }
+};
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+void cdl_options_default(cdl_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->hash_load = 0.5;
+  o->radix_bits = 8;
+}
+
+cdl_status cdl_create(const cdl_options* opts, cdl_engine** out) {
+  if (!out) return CDL_E_INVALID;
+  *out = nullptr;
+  auto e = std::make_unique<cdl_engine>();
+  if (opts) e->opt = *opts;
+  else cdl_options_default(&e->opt);
+  e->st = static_cast<cudaStream_t>(e->opt.stream);
+  e->pool.af = e->opt.alloc;
+  e->pool.ff = e->opt.free;
+  e->pool.ctx = e->opt.alloc_ctx;
+  e->pool.limit = e->opt.mem_limit;
+  e->hash_load = (e->opt.hash_load > 0 && e->opt.hash_load <= 0.9) ? e->opt.hash_load : 0.5;
+  e->radix_bits = e->opt.radix_bits == 10 ? 10 : 8;
+  e->prof.on = e->opt.timing != 0;
+  if ((e->opt.alloc == nullptr) != (e->opt.free == nullptr)) return CDL_E_INVALID;
+  e->ctl = e->alloc(kCtlSlots * sizeof(uint64_t));
+  if (!e->ctl.p) return CDL_E_NOMEM;
+  if (cudaMallocHost(&e->h_ctl, kCtlSlots * sizeof(uint64_t)) != cudaSuccess) {
+    cudaGetLastError();
+    e->h_ctl = nullptr;
+    return CDL_E_CUDA;
+  }
+  if (cudaMemsetAsync(e->ctl.p, 0, kCtlSlots * sizeof(uint64_t), e->st) != cudaSuccess)
+    return CDL_E_CUDA;
+  e->ctx.st = e->st;
+  e->ctx.d_err = reinterpret_cast<uint32_t*>(e->dslot(kSlotErr));
+  e->ctx.prof = &e->prof;
+  if (e->opt.spin_limit) e->ctx.spin_limit = e->opt.spin_limit;
+  *out = e.release();
+  return CDL_OK;
+}
+
+cdl_status cdl_destroy(cdl_engine* e) {
+  if (!e) return CDL_OK;
+  cudaStreamSynchronize(e->st);
+  delete e;
+  return CDL_OK;
+}
+
+cdl_status cdl_relation_create(cdl_engine* e, const char* name, uint32_t arity, cdl_rel* out) {
+  if (!e || !name || !out) return CDL_E_INVALID;
+  if (e->ran) return e->fail(CDL_E_STATE, "relations must precede cdl_run");
+  if (arity < 1 || arity > CDL_MAX_ARITY) return e->fail(CDL_E_INVALID, "arity must be 1..4");
+  if (e->by_name.count(name)) return e->fail(CDL_E_INVALID, std::string("duplicate relation ") + name);
+  if (e->rels.size() >= kMaxRels) return e->fail(CDL_E_INVALID, "too many relations");
+  auto r = std::make_unique<Relation>();
+  r->name = name;
+  r->arity = arity;
+  r->full.k = r->delta.k = r->fresh.k = arity;
+  *out = (cdl_rel)e->rels.size();
+  e->by_name[name] = *out;
+  e->rels.push_back(std::move(r));
+  return CDL_OK;
+}
+
+cdl_status cdl_relation_load(cdl_engine* e, cdl_rel rel, const uint32_t* const* cols, uint64_t n,
+                             int on_device) {
+  if (!e || (!cols && n)) return CDL_E_INVALID;
+  if (rel >= e->rels.size()) return e->fail(CDL_E_INVALID, "no such relation");
+  return e->load(rel, cols, n, on_device);
+}
+
+cdl_status cdl_rule_add(cdl_engine* e, const cdl_rule* rule) {
+  if (!e || !rule) return CDL_E_INVALID;
+  if (e->ran) return e->fail(CDL_E_STATE, "rules must precede cdl_run");
+  if (rule->nbody < 1 || rule->nbody > CDL_MAX_BODY || !rule->body)
+    return e->fail(CDL_E_INVALID, "a rule needs 1..4 body atoms");
+  auto conv = [&](const cdl_atom& a, AtomR& out) -> bool {
+    if (a.rel >= e->rels.size() || a.arity != e->rels[a.rel]->arity || !a.terms) return false;
+    out.rel = a.rel;
+    for (uint32_t k = 0; k < a.arity; ++k) {
+      if (a.terms[k].is_const && a.terms[k].v == CDL_EMPTY_KEY) return false;
+      out.t.push_back(Term{a.terms[k].is_const != 0, a.terms[k].v});
+    }
+    return true;
+  };
+  RuleR r;
+  if (!conv(rule->head, r.head)) return e->fail(CDL_E_INVALID, "bad head atom");
+  std::vector<uint32_t> body_vars;
+  for (uint32_t i = 0; i < rule->nbody; ++i) {
+    AtomR a;
+    if (!conv(rule->body[i], a)) return e->fail(CDL_E_INVALID, "bad body atom");
+    for (const Term& t : a.t)
+      if (!t.is_const) body_vars.push_back(t.v);
+    r.body.push_back(a);
+  }
+  auto bound = [&](uint32_t v) {
+    return std::find(body_vars.begin(), body_vars.end(), v) != body_vars.end();
+  };
+  for (const Term& t : r.head.t)
+    if (!t.is_const && !bound(t.v)) return e->fail(CDL_E_INVALID, "head variable not in body");
+  if (rule->nneq > 4 || (rule->nneq && !rule->neq)) return e->fail(CDL_E_INVALID, "bad inequalities");
+  for (uint32_t i = 0; i < rule->nneq; ++i) {
+    const uint32_t a = rule->neq[2 * i], b = rule->neq[2 * i + 1];
+    if (!bound(a) || !bound(b)) return e->fail(CDL_E_INVALID, "inequality variable not in body");
+    r.neq.emplace_back(a, b);
+  }
+  e->rules.push_back(std::move(r));
+  return CDL_OK;
+}
+
+cdl_status cdl_run(cdl_engine* e, cdl_stats* stats) {
+  if (!e) return CDL_E_INVALID;
+  return e->run(stats);
+}
+
+cdl_status cdl_relation_size(cdl_engine* e, cdl_rel rel, uint64_t* n) {
+  if (!e || !n) return CDL_E_INVALID;
+  if (rel >= e->rels.size()) return e->fail(CDL_E_INVALID, "no such relation");
+  *n = e->rels[rel]->full.n;
+  return CDL_OK;
+}
+
+cdl_status cdl_relation_export(cdl_engine* e, cdl_rel rel, uint32_t* const* cols, uint64_t cap,
+                               uint64_t* n_written, int on_device) {
+  if (!e || !n_written) return CDL_E_INVALID;
+  if (rel >= e->rels.size()) return e->fail(CDL_E_INVALID, "no such relation");
+  const Relation& R = *e->rels[rel];
+  *n_written = R.full.n;
+  if (cap < R.full.n) return e->fail(CDL_E_CAPACITY, "export buffer too small");
+  if (R.full.n == 0) return CDL_OK;
+  if (!cols) return CDL_E_INVALID;
+  for (uint32_t k = 0; k < R.arity; ++k) {
+    if (!cols[k]) return e->fail(CDL_E_INVALID, "null column pointer");
+    cudaError_t er = cudaMemcpyAsync(cols[k], R.full.c[k], R.full.n * 4,
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                     e->st);
+    if (er != cudaSuccess) return e->cuda_fail(er, "export");
+  }
+  cudaError_t er = cudaStreamSynchronize(e->st);
+  return er == cudaSuccess ? CDL_OK : e->cuda_fail(er, "export");
+}
+
+cdl_status cdl_kernel_profile(cdl_engine* e, uint32_t idx, char* name, size_t name_cap,
+                              uint64_t* launches, double* ms, double* bytes) {
+  if (!e) return CDL_E_INVALID;
+  if (idx >= (uint32_t)kNumClasses) return CDL_E_INVALID;
+  if (name && name_cap) {
+    std::strncpy(name, kernel_class_name((int)idx), name_cap - 1);
+    name[name_cap - 1] = 0;
+  }
+  if (launches) *launches = e->prof.launches[idx];
+  if (ms) *ms = e->prof.ms[idx];
+  if (bytes) *bytes = e->prof.bytes[idx];
+  return CDL_OK;
+}
+
+const char* cdl_last_error(const cdl_engine* e) { return e ? e->err.c_str() : "no engine"; }
+
+}  // extern "C"

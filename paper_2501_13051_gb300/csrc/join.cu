@@ -1,0 +1,235 @@
+// Step (b): the join of Algorithm 1 in three passes.
+//
+// Pass 1 (count): every probe row looks its key up in the build side's
+// hybrid index and stores the matched range length (0 when absent), and
+// each tile of rows also sums its lengths -- the first half of the scan.
+// Pass 2 (scan): exclusive scan of the lengths into 64-bit output offsets
+// (pos_buf) and the total join size (Algorithm 1's reduce).
+// Pass 3 (write): output-partitioned, the variant Section 4 chooses for
+// skew: each block owns an equal share of the merged sequence of (row
+// starts, output positions) -- a merge-path split found by binary search
+// over the offsets, so a block's work is bounded whether its rows match
+// nothing or one row matches a hundred thousand tuples.  The block re-probes
+// the index once per row it covers, then every output position finds its row
+// by binary search in shared memory (the search of Algorithm 1's write loop,
+// over the non-empty ranges only) and gathers the build row
+// start + (n - pos_buf[j]).  Projection, constant head columns, equalities
+// beyond the hashed key and inequalities (x != y) are applied in the same
+// pass, so the join result is written directly as head columns (Section 4:
+// the join result is materialised only at projection).
+#include "kernels.h"
+
+namespace cdl {
+
+namespace {
+
+constexpr int kCT = 256;  // count pass: threads; tiles of kScanTile rows
+constexpr int kCItems = kScanTile / kCT;
+constexpr int kJT = 256;  // write pass threads
+constexpr int kJItems = 8;
+constexpr int kJTile = kJT * kJItems;  // merged items per block
+
+__device__ __forceinline__ uint32_t probe_key1(const JoinSpec& j, uint64_t row) {
+  return j.pk1 == 0xFFu ? 0u : __ldg(j.probe.c[j.pk1] + row);
+}
+
+// Range of build rows matching probe row `row`: the hybrid index lookup, or
+// every build row for a join without shared variables.
+__device__ __forceinline__ uint32_t lookup(const JoinSpec& j, uint64_t mask, uint64_t row,
+                                          uint32_t* start) {
+  if (j.cross) {
+    *start = 0;
+    return j.n_build;
+  }
+  return probe_table(j.table, mask, __ldg(j.probe.c[j.pk0] + row), probe_key1(j, row), start);
+}
+
+__global__ void __launch_bounds__(kCT) k_join_count(const JoinSpec j, uint32_t* __restrict__ counts,
+                                                    uint64_t* __restrict__ tile_sums) {
+  __shared__ uint64_t red[kCT / 32 + 1];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  const uint64_t mask = j.slots - 1;
+  uint64_t s = 0;
+#pragma unroll 4
+  for (int i = 0; i < kCItems; ++i) {
+    const uint64_t row = base + (uint64_t)i * kCT + threadIdx.x;
+    if (row < j.n_probe) {
+      uint32_t st;
+      const uint32_t cnt = lookup(j, mask, row, &st);
+      counts[row] = cnt;
+      s += cnt;
+    }
+  }
+  uint64_t total;
+  block_exclusive_sum<kCT, uint64_t>(s, red, &total);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kCT) k_join_count_only(const JoinSpec j,
+                                                         uint32_t* __restrict__ counts) {
+  const uint64_t row = (uint64_t)blockIdx.x * kCT + threadIdx.x;
+  if (row >= j.n_probe) return;
+  uint32_t st;
+  counts[row] = lookup(j, j.slots - 1, row, &st);
+}
+
+// Number of probe rows among the first d items of the merge of the row
+// starts off[0..n) with the output positions 0..total-1 (a row start goes
+// before the output positions it is <=).
+__device__ __forceinline__ uint64_t merge_split(const uint64_t* off, uint64_t n, uint64_t total,
+                                                uint64_t d) {
+  uint64_t lo = d > total ? d - total : 0, hi = d < n ? d : n;
+  while (lo < hi) {
+    const uint64_t mid = lo + ((hi - lo) >> 1);
+    if (__ldg(off + mid) <= d - mid - 1)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t ref_value(const JoinSpec& j, const Ref& r, uint64_t row,
+                                              uint64_t brow) {
+  if (r.side == 0) return __ldg(j.probe.c[r.v] + row);
+  if (r.side == 1) return __ldg(j.build.c[r.v] + brow);
+  return r.v;
+}
+
+template <bool FILTER>
+__global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint64_t* __restrict__ off,
+                                                    uint64_t total, ColsOut out, uint64_t base,
+                                                    unsigned long long* cursor, uint64_t out_cap,
+                                                    uint32_t* err) {
+  __shared__ uint64_t s_off[kJTile + 1];
+  __shared__ uint32_t s_start[kJTile + 1];
+  __shared__ uint64_t s_split[2];
+  __shared__ uint32_t red[kJT / 32 + 1];
+  __shared__ unsigned long long s_base;
+  const uint64_t nm = j.n_probe + total;
+  const uint64_t d0 = (uint64_t)blockIdx.x * kJTile;
+  const uint64_t d1 = d0 + kJTile < nm ? d0 + kJTile : nm;
+  if (threadIdx.x == 0) s_split[0] = merge_split(off, j.n_probe, total, d0);
+  if (threadIdx.x == 32) s_split[1] = merge_split(off, j.n_probe, total, d1);
+  if (!FILTER && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(cursor, (unsigned long long)total);
+  __syncthreads();
+  const uint64_t j0 = s_split[0], j1 = s_split[1];
+  const uint64_t o0 = d0 - j0, o1 = d1 - j1;
+  const uint64_t r_lo = j0 > 0 ? j0 - 1 : 0;
+  const uint32_t nrows = (uint32_t)(j1 - r_lo);
+  const uint64_t mask = j.slots - 1;
+  for (uint32_t r = threadIdx.x; r < nrows; r += kJT) {
+    const uint64_t row = r_lo + r;
+    const uint64_t a = __ldg(off + row);
+    const uint64_t b = row + 1 < j.n_probe ? __ldg(off + row + 1) : total;
+    uint32_t st = 0;
+    if (b > a) lookup(j, mask, row, &st);
+    s_off[r] = a;
+    s_start[r] = st;
+  }
+  __syncthreads();
+  for (uint64_t ob = o0; ob < o1; ob += kJT) {
+    const uint64_t o = ob + threadIdx.x;
+    const bool valid = o < o1;
+    uint32_t vals[kMaxK] = {0, 0, 0, 0};
+    bool keep = valid;
+    if (valid) {
+      uint32_t lo = 0, hi = nrows;  // largest r with s_off[r] <= o
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_off[mid] <= o)
+          lo = mid;
+        else
+          hi = mid;
+      }
+      const uint64_t row = r_lo + lo;
+      const uint64_t brow = (uint64_t)s_start[lo] + (o - s_off[lo]);
+#pragma unroll
+      for (int k = 0; k < kMaxK; ++k)
+        if (k < (int)j.out_k) vals[k] = ref_value(j, j.out[k], row, brow);
+      if (FILTER) {
+        for (uint32_t q = 0; q < j.n_eq; ++q)
+          keep &= ref_value(j, j.eq[q][0], row, brow) == ref_value(j, j.eq[q][1], row, brow);
+        for (uint32_t q = 0; q < j.n_neq; ++q)
+          keep &= ref_value(j, j.neq[q][0], row, brow) != ref_value(j, j.neq[q][1], row, brow);
+      }
+    }
+    uint64_t pos;
+    if (FILTER) {
+      uint32_t cnt;
+      const uint32_t local = block_exclusive_sum<kJT, uint32_t>(keep ? 1u : 0u, red, &cnt);
+      if (threadIdx.x == 0) s_base = cnt ? atomicAdd(cursor, (unsigned long long)cnt) : 0ull;
+      __syncthreads();
+      pos = s_base + local;
+      __syncthreads();
+    } else {
+      pos = base + o;
+    }
+    if (keep) {
+      if (pos < out_cap) {
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k)
+          if (k < (int)j.out_k) out.c[k][pos] = vals[k];
+      } else {
+        if (err) atomicOr(err, kErrCapacity);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t join_count_only(Ctx& c, const JoinSpec& j, uint32_t* counts) {
+  if (j.n_probe == 0) return cudaSuccess;
+  ProfScope p(c, kJoinCount, (j.pk1 == 0xFFu ? 4.0 : 8.0) * j.n_probe + 20.0 * j.n_probe);
+  k_join_count_only<<<(unsigned)((j.n_probe + kCT - 1) / kCT), kCT, 0, c.st>>>(j, counts);
+  return cudaGetLastError();
+}
+
+size_t join_count_workspace(uint64_t n_probe) {
+  const size_t counts = ((n_probe * sizeof(uint32_t)) + 255) & ~size_t(255);
+  return counts + scan_workspace(n_probe);
+}
+
+cudaError_t join_count_scan(Ctx& c, const JoinSpec& j, uint64_t* d_off, uint64_t* d_total,
+                            void* ws) {
+  if (j.n_probe == 0) return cudaMemsetAsync(d_total, 0, sizeof(uint64_t), c.st);
+  uint32_t* counts = static_cast<uint32_t*>(ws);
+  void* scan_ws = static_cast<char*>(ws) + (((j.n_probe * sizeof(uint32_t)) + 255) & ~size_t(255));
+  const uint64_t tiles = (j.n_probe + kScanTile - 1) / kScanTile;
+  {
+    const double keyb = j.pk1 == 0xFFu ? 4.0 : 8.0;
+    ProfScope p(c, kJoinCount, (keyb + 16.0 + 4.0) * j.n_probe);
+    k_join_count<<<(unsigned)tiles, kCT, 0, c.st>>>(j, counts, static_cast<uint64_t*>(scan_ws));
+  }
+  return scan_finish(c, counts, j.n_probe, d_off, d_total, scan_ws);
+}
+
+cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_t total,
+                       ColsOut out, uint64_t base, uint64_t* d_cursor, uint64_t out_cap) {
+  if (total == 0 || j.n_probe == 0) return cudaSuccess;
+  const uint64_t nm = j.n_probe + total;
+  const uint64_t blocks = (nm + kJTile - 1) / kJTile;
+  const bool filter = j.n_neq > 0 || j.n_eq > 0;
+  // offsets + re-probe per row, build gather per build column read, head write
+  // per probe row: two offsets, key, re-probed slot, its own head columns;
+  // per output: the gathered build columns and the written head columns
+  uint32_t nbuild = 0, nprobe = 0;
+  for (uint32_t k = 0; k < j.out_k; ++k) {
+    nbuild += j.out[k].side == 1;
+    nprobe += j.out[k].side == 0;
+  }
+  const double bytes = (16.0 + 4.0 + 16.0 + 4.0 * nprobe) * j.n_probe +
+                       (4.0 * nbuild + 4.0 * j.out_k) * total;
+  ProfScope p(c, kJoinWrite, bytes);
+  auto* cur = reinterpret_cast<unsigned long long*>(d_cursor);
+  if (filter)
+    k_join_write<true><<<(unsigned)blocks, kJT, 0, c.st>>>(j, d_off, total, out, base, cur, out_cap,
+                                                          c.d_err);
+  else
+    k_join_write<false><<<(unsigned)blocks, kJT, 0, c.st>>>(j, d_off, total, out, base, cur,
+                                                           out_cap, c.d_err);
+  return cudaGetLastError();
+}
+
+}  // namespace cdl

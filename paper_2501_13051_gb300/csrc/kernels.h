@@ -1,0 +1,179 @@
+// Host-side launchers of the round's kernels (internal to libcdl).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cdl {
+
+// ---------------------------------------------------------------- profiling
+// Kernel classes timed separately when the engine runs with timing on.
+enum KernelClass : int {
+  kHashBuild = 0,
+  kCountHeads,
+  kJoinCount,
+  kScan,
+  kJoinWrite,
+  kRadixUpsweep,
+  kRadixScatter,
+  kDiffCount,
+  kDiffMerge,
+  kSelect,
+  kMisc,
+  kNumClasses
+};
+const char* kernel_class_name(int c);
+
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<Rec> open;
+  std::vector<cudaEvent_t> pool;
+  uint64_t launches[kNumClasses] = {};
+  double ms[kNumClasses] = {};
+  double bytes[kNumClasses] = {};
+  uint64_t total_launches = 0;
+  double total_bytes = 0;
+  cudaEvent_t get();
+  void begin(int cls, cudaStream_t st);
+  void end(int cls, double algo_bytes, cudaStream_t st);
+  void add_bytes(int cls, double b);  // adds to the latest launch of cls
+  void collect();  // waits for recorded events and sums their times
+  void reset();
+  ~Profiler();
+};
+
+// Launch context: stream, device error word, profiler (may be null).
+struct Ctx {
+  cudaStream_t st = nullptr;
+  uint32_t* d_err = nullptr;
+  Profiler* prof = nullptr;
+  uint64_t spin_limit = 1ull << 26;
+};
+
+struct ProfScope {
+  Ctx& c;
+  int cls;
+  double bytes;
+  ProfScope(Ctx& ctx, int k, double b) : c(ctx), cls(k), bytes(b) {
+    if (c.prof) c.prof->begin(cls, c.st);
+  }
+  ~ProfScope() {
+    if (c.prof) c.prof->end(cls, bytes, c.st);
+  }
+};
+
+// -------------------------------------------------------------------- hash
+uint64_t table_slots(uint64_t n_keys, double load);
+// keys: columns k0 (and k1 when non-null) sorted lexicographically, n rows.
+cudaError_t hash_build(Ctx& c, const uint32_t* k0, const uint32_t* k1, uint64_t n, Slot* table,
+                       uint64_t slots);
+// Number of distinct (k0, k1) keys of a sorted column pair into *d_out.
+cudaError_t count_heads(Ctx& c, const uint32_t* k0, const uint32_t* k1, uint64_t n,
+                        uint64_t* d_out);
+
+// -------------------------------------------------------------------- scan
+constexpr int kScanTile = 2048;  // elements per scan tile
+size_t scan_workspace(uint64_t n);
+// out[i] = sum in[0..i); *d_total = sum of all (device pointer, may be null).
+cudaError_t exclusive_scan(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out,
+                           uint64_t* d_total, void* ws);
+// Second half of the scan when ws already holds the sums of kScanTile tiles.
+cudaError_t scan_finish(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* d_total,
+                        void* ws);
+
+// -------------------------------------------------------------------- join
+struct Ref {
+  uint8_t side;  // 0 probe, 1 build, 2 constant
+  uint32_t v;
+};
+struct JoinSpec {
+  ColsIn probe;
+  uint64_t n_probe;
+  uint32_t pk0, pk1;  // probe key columns; pk1 = 0xFF when the key has one word
+  ColsIn build;       // sorted by the key columns bk0 (, bk1)
+  const Slot* table;
+  uint64_t slots;
+  uint32_t out_k;
+  Ref out[kMaxK];
+  uint32_t n_neq;
+  Ref neq[4][2];
+  uint32_t n_eq;  // extra equalities (join keys beyond two words)
+  Ref eq[4][2];
+  uint32_t cross;    // 1: no shared variable, every build row matches
+  uint32_t n_build;  // build rows (used by cross joins)
+};
+size_t join_count_workspace(uint64_t n_probe);
+// Pass 1 alone: counts[i] for every probe row.
+cudaError_t join_count_only(Ctx& c, const JoinSpec& j, uint32_t* counts);
+// Pass 1 + 2: counts and exclusive offsets of every probe row; total in *d_total.
+cudaError_t join_count_scan(Ctx& c, const JoinSpec& j, uint64_t* d_off, uint64_t* d_total,
+                            void* ws);
+// Pass 3: writes the output tuples.  With no filters, tuple o goes to
+// out[base + o] and *d_cursor grows by total; with filters, survivors are
+// packed at *d_cursor (atomic).  out_cap bounds every write.
+cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_t total,
+                       ColsOut out, uint64_t base, uint64_t* d_cursor, uint64_t out_cap);
+
+// -------------------------------------------------------------------- sort
+// Digit plan of an LSD radix sort over the packed key of K columns.
+struct RadixPlan {
+  uint32_t k = 0;
+  uint32_t bits = 8;
+  uint32_t npass = 0;
+  struct Pass {
+    uint32_t sh[kMaxK], mask[kMaxK], dsh[kMaxK];
+  };
+  std::vector<Pass> pass;
+};
+// col_bits[k]: significant bits of column k (all values < 2^col_bits[k]).
+RadixPlan make_radix_plan(uint32_t k, const uint32_t* col_bits, uint32_t digit_bits);
+size_t radix_workspace(uint64_t n, uint32_t digit_bits);
+// Sorts (a, n rows) using b as the alternate buffer; returns in *in_b
+// whether the result ended in b.
+cudaError_t radix_sort(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t n, void* ws,
+                       bool* in_b);
+// Column maxima into d_max[k] (for plans of unknown data).
+cudaError_t column_max(Ctx& c, ColsIn in, uint32_t k, uint64_t n, uint32_t* d_max);
+
+// ------------------------------------------------------------------ setops
+size_t diff_merge_workspace(uint64_t n_full, uint64_t n_fresh);
+// delta = fresh - full, merged = full U delta; *d_ndelta receives |delta|.
+// When merged.c[0] is null only delta is produced.
+cudaError_t diff_merge(Ctx& c, uint32_t k, ColsIn full, uint64_t n_full, ColsIn fresh,
+                       uint64_t n_fresh, ColsOut delta, ColsOut merged, uint64_t* d_ndelta,
+                       void* ws);
+
+// Selection + projection of one atom: keeps rows with col == const, col ==
+// col and (on output refs) out != out; writes out tuples packed at
+// *d_cursor (atomic).  Refs use side 0 (input column) or 2 (constant).
+struct SelectSpec {
+  ColsIn in;
+  uint32_t in_k;
+  uint64_t n;
+  uint32_t n_const;
+  uint32_t const_col[kMaxK];
+  uint32_t const_val[kMaxK];
+  uint32_t n_same;
+  uint32_t same[kMaxK][2];
+  uint32_t out_k;
+  Ref out[kMaxK];
+  uint32_t n_neq;
+  Ref neq[4][2];
+};
+cudaError_t select_project(Ctx& c, const SelectSpec& s, ColsOut out, uint64_t* d_cursor,
+                           uint64_t out_cap);
+
+// Reserved-value check and column maxima of loaded data.
+cudaError_t check_values(Ctx& c, ColsIn in, uint32_t k, uint64_t n, uint32_t* d_max);
+
+}  // namespace cdl

@@ -1,0 +1,120 @@
+// Exclusive scan of uint32 counts into uint64 offsets (Algorithm 1's
+// pos_buf) by reduce-then-scan: per-tile sums, one block scanning the tile
+// sums, then a per-tile scan seeded with the tile's prefix.  No inter-block
+// waiting, so no kernel here can stall on another block.
+#include "kernels.h"
+
+namespace cdl {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+static_assert(kScanTile == kScanThreads * kScanItems, "scan tile");
+constexpr int kTopThreads = 1024;
+
+__host__ __device__ constexpr uint32_t pad_idx(uint32_t i) { return i + (i >> 5); }
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in,
+                                                              uint64_t n,
+                                                              uint64_t* __restrict__ tile_sums) {
+  __shared__ uint64_t red[kScanThreads / 32 + 1];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  uint64_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const uint64_t idx = base + (uint64_t)i * kScanThreads + threadIdx.x;
+    if (idx < n) s += __ldg(in + idx);
+  }
+  uint64_t total;
+  block_exclusive_sum<kScanThreads, uint64_t>(s, red, &total);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of ntiles tile sums in place; total -> *d_total.
+__global__ void __launch_bounds__(kTopThreads) k_scan_top(uint64_t* __restrict__ sums,
+                                                          uint64_t ntiles,
+                                                          uint64_t* __restrict__ d_total) {
+  __shared__ uint64_t red[kTopThreads / 32 + 1];
+  uint64_t carry = 0;
+  for (uint64_t b = 0; b < ntiles; b += kTopThreads) {
+    const uint64_t i = b + threadIdx.x;
+    const uint64_t v = i < ntiles ? sums[i] : 0;
+    uint64_t tot;
+    const uint64_t ex = block_exclusive_sum<kTopThreads, uint64_t>(v, red, &tot);
+    if (i < ntiles) sums[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && d_total) *d_total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ in,
+                                                             uint64_t n,
+                                                             const uint64_t* __restrict__ prefix,
+                                                             uint64_t* __restrict__ out) {
+  __shared__ uint32_t s_in[pad_idx(kScanTile) + 1];
+  __shared__ uint64_t red[kScanThreads / 32 + 1];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  // striped, coalesced load into shared memory
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const uint32_t l = i * kScanThreads + threadIdx.x;
+    const uint64_t idx = base + l;
+    s_in[pad_idx(l)] = idx < n ? __ldg(in + idx) : 0u;
+  }
+  __syncthreads();
+  // blocked: thread t owns tile elements [t*ITEMS, (t+1)*ITEMS)
+  uint32_t v[kScanItems];
+  uint64_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = s_in[pad_idx(threadIdx.x * kScanItems + i)];
+    s += v[i];
+  }
+  uint64_t tot;
+  uint64_t run = block_exclusive_sum<kScanThreads, uint64_t>(s, red, &tot) + prefix[blockIdx.x];
+  const uint64_t first = base + (uint64_t)threadIdx.x * kScanItems;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (first + i < n) out[first + i] = run;
+    run += v[i];
+  }
+}
+
+}  // namespace
+
+size_t scan_workspace(uint64_t n) {
+  const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+  return ((tiles + 1) * sizeof(uint64_t) + 255) & ~size_t(255);
+}
+
+cudaError_t exclusive_scan(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out,
+                           uint64_t* d_total, void* ws) {
+  if (n == 0) {
+    if (d_total) return cudaMemsetAsync(d_total, 0, sizeof(uint64_t), c.st);
+    return cudaSuccess;
+  }
+  const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+  uint64_t* sums = static_cast<uint64_t*>(ws);
+  {
+    ProfScope p(c, kScan, 4.0 * n);
+    k_scan_reduce<<<(unsigned)tiles, kScanThreads, 0, c.st>>>(in, n, sums);
+  }
+  return scan_finish(c, in, n, out, d_total, ws);
+}
+
+cudaError_t scan_finish(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* d_total,
+                        void* ws) {
+  if (n == 0) {
+    if (d_total) return cudaMemsetAsync(d_total, 0, sizeof(uint64_t), c.st);
+    return cudaSuccess;
+  }
+  const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+  uint64_t* sums = static_cast<uint64_t*>(ws);
+  ProfScope p(c, kScan, 4.0 * n + 8.0 * n);
+  k_scan_top<<<1, kTopThreads, 0, c.st>>>(sums, tiles, d_total);
+  k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, c.st>>>(in, n, sums, out);
+  return cudaGetLastError();
+}
+
+}  // namespace cdl

@@ -1,0 +1,285 @@
+// Step (c): LSD radix sort of tuples stored as separate uint32 columns
+// (Section 5: per-column storage lets tuples be radix-sorted instead of
+// merge-sorted).  The key of a tuple is its columns concatenated, column 0
+// most significant, each column trimmed to its significant bits; passes take
+// `bits`-wide digits of that packed key from the least significant end, so a
+// relation over ids < 2^18 sorts in ceil(36 / 8) = 5 passes instead of 8.
+//
+// Each pass: (1) every tile of 4096 tuples counts its digits in shared
+// memory; (2) an exclusive scan over the digit-major [digit][tile] counts
+// gives every (digit, tile) run its global start; (3) every tile ranks its
+// tuples stably (warp-level match on the digit, warps in order) and writes
+// them through a shared-memory staging buffer so each digit's run leaves as
+// contiguous stores.  Stable passes from least to most significant digit give
+// the lexicographic order.
+#include "kernels.h"
+
+namespace cdl {
+
+namespace {
+
+constexpr int kRT = 256;
+constexpr int kRItems = 16;
+constexpr int kRTile = kRT * kRItems;
+constexpr int kRW = kRT / 32;
+
+struct PassP {
+  uint32_t sh[kMaxK], mask[kMaxK], dsh[kMaxK];
+};
+
+template <int K>
+__device__ __forceinline__ uint32_t digit_of(const uint32_t (&v)[K], const PassP& p) {
+  uint32_t d = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) d |= ((v[k] >> p.sh[k]) & p.mask[k]) << p.dsh[k];
+  return d;
+}
+
+template <int K, int BITS>
+__global__ void __launch_bounds__(kRT) k_radix_upsweep(ColsIn in, uint64_t n, PassP p,
+                                                       uint32_t* __restrict__ tile_hist,
+                                                       uint64_t ntiles) {
+  constexpr int R = 1 << BITS;
+  __shared__ uint32_t h[R];
+  for (int i = threadIdx.x; i < R; i += kRT) h[i] = 0;
+  __syncthreads();
+  const uint64_t base = (uint64_t)blockIdx.x * kRTile;
+#pragma unroll 4
+  for (int it = 0; it < kRItems; ++it) {
+    const uint64_t idx = base + (uint64_t)it * kRT + threadIdx.x;
+    if (idx < n) {
+      uint32_t v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = p.mask[k] ? __ldg(in.c[k] + idx) : 0u;
+      atomicAdd(&h[digit_of<K>(v, p)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < R; i += kRT) tile_hist[(uint64_t)i * ntiles + blockIdx.x] = h[i];
+}
+
+template <int K, int BITS>
+__global__ void __launch_bounds__(kRT) k_radix_scatter(ColsIn in, ColsOut out, uint64_t n, PassP p,
+                                                       const uint64_t* __restrict__ off,
+                                                       uint64_t ntiles) {
+  constexpr int R = 1 << BITS;
+  constexpr int DPT = (R + kRT - 1) / kRT;
+  __shared__ uint32_t wh[kRW][R];  // per-warp digit counts, then per-warp offsets
+  __shared__ uint32_t tstart[R];   // tile-local start of each digit's run
+  __shared__ uint64_t gstart[R];   // global start of this tile's run of each digit
+  __shared__ uint32_t red[kRT / 32 + 1];
+  extern __shared__ uint32_t stage[];  // K x kRTile
+  for (int i = threadIdx.x; i < kRW * R; i += kRT) (&wh[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const uint64_t base = (uint64_t)blockIdx.x * kRTile;
+  const uint64_t wbase = base + (uint64_t)warp * 32 * kRItems;
+  uint32_t v[kRItems][K];
+  uint32_t rk[kRItems];
+#pragma unroll
+  for (int it = 0; it < kRItems; ++it) {
+    const uint64_t idx = wbase + (uint64_t)it * 32 + lane;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[it][k] = idx < n ? __ldg(in.c[k] + idx) : 0u;
+  }
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int it = 0; it < kRItems; ++it) {
+    const uint64_t idx = wbase + (uint64_t)it * 32 + lane;
+    const bool valid = idx < n;
+    const uint32_t d = valid ? digit_of<K>(v[it], p) : (uint32_t)R;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t before = __popc(peers & lt);
+    uint32_t b = 0;
+    if (valid) b = wh[warp][d];
+    __syncwarp();
+    if (valid && before == 0) wh[warp][d] = b + __popc(peers);
+    __syncwarp();
+    rk[it] = b + before;
+  }
+  __syncthreads();
+  // per digit: exclusive offsets across warps (warp order = input order)
+  for (int d = threadIdx.x; d < R; d += kRT) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kRW; ++w) {
+      const uint32_t t = wh[w][d];
+      wh[w][d] = s;
+      s += t;
+    }
+    tstart[d] = s;
+    gstart[d] = off[(uint64_t)d * ntiles + blockIdx.x];
+  }
+  __syncthreads();
+  {  // tile-local digit starts: exclusive scan of the digit totals
+    uint32_t loc[DPT];
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      const int d = threadIdx.x * DPT + q;
+      loc[q] = d < R ? tstart[d] : 0u;
+      s += loc[q];
+    }
+    uint32_t tot;
+    uint32_t ex = block_exclusive_sum<kRT, uint32_t>(s, red, &tot);
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      const int d = threadIdx.x * DPT + q;
+      if (d < R) tstart[d] = ex;
+      ex += loc[q];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kRItems; ++it) {
+    const uint64_t idx = wbase + (uint64_t)it * 32 + lane;
+    if (idx < n) {
+      const uint32_t d = digit_of<K>(v[it], p);
+      const uint32_t pos = tstart[d] + wh[warp][d] + rk[it];
+#pragma unroll
+      for (int k = 0; k < K; ++k) stage[k * kRTile + pos] = v[it][k];
+    }
+  }
+  __syncthreads();
+  const uint32_t tile_n = (uint32_t)(n - base < (uint64_t)kRTile ? n - base : kRTile);
+  for (uint32_t i = threadIdx.x; i < tile_n; i += kRT) {
+    uint32_t t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = stage[k * kRTile + i];
+    const uint32_t d = digit_of<K>(t, p);
+    const uint64_t g = gstart[d] + (i - tstart[d]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) out.c[k][g] = t[k];
+  }
+}
+
+__global__ void k_column_max(ColsIn in, uint32_t k, uint64_t n, uint32_t* d_max) {
+  for (uint32_t c = 0; c < k; ++c) {
+    uint32_t m = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+      m = max(m, __ldg(in.c[c] + i));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane_id() == 0) atomicMax(d_max + c, m);
+  }
+}
+
+template <int K, int BITS>
+cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t n, void* ws,
+                        bool* in_b) {
+  constexpr int R = 1 << BITS;
+  const uint64_t ntiles = (n + kRTile - 1) / kRTile;
+  const uint64_t cells = (uint64_t)R * ntiles;
+  uint32_t* hist = static_cast<uint32_t*>(ws);
+  uint64_t* off = reinterpret_cast<uint64_t*>(static_cast<char*>(ws) +
+                                              ((cells * 4 + 255) & ~uint64_t(255)));
+  void* scan_ws = reinterpret_cast<char*>(off) + ((cells * 8 + 255) & ~uint64_t(255));
+  const size_t smem = sizeof(uint32_t) * K * kRTile;
+  cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<K, BITS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  ColsOut src = a, dst = b;
+  bool flip = false;
+  for (uint32_t pi = 0; pi < plan.npass; ++pi) {
+    PassP p;
+    for (int k = 0; k < kMaxK; ++k) {
+      p.sh[k] = plan.pass[pi].sh[k];
+      p.mask[k] = plan.pass[pi].mask[k];
+      p.dsh[k] = plan.pass[pi].dsh[k];
+    }
+    ColsIn in;
+    for (int k = 0; k < kMaxK; ++k) in.c[k] = src.c[k];
+    uint32_t cols_used = 0;
+    for (int k = 0; k < K; ++k) cols_used += p.mask[k] != 0;
+    {
+      ProfScope ps(c, kRadixUpsweep, 4.0 * cols_used * n + 4.0 * cells);
+      k_radix_upsweep<K, BITS><<<(unsigned)ntiles, kRT, 0, c.st>>>(in, n, p, hist, ntiles);
+    }
+    e = exclusive_scan(c, hist, cells, off, nullptr, scan_ws);
+    if (e != cudaSuccess) return e;
+    {
+      ProfScope ps(c, kRadixScatter, 8.0 * K * n);
+      k_radix_scatter<K, BITS><<<(unsigned)ntiles, kRT, smem, c.st>>>(in, dst, n, p, off, ntiles);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    std::swap(src, dst);
+    flip = !flip;
+  }
+  *in_b = flip;
+  return cudaSuccess;
+}
+
+template <int K>
+cudaError_t sort_k(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t n, void* ws,
+                   bool* in_b) {
+  switch (plan.bits) {
+    case 8: return sort_passes<K, 8>(c, plan, a, b, n, ws, in_b);
+    case 10: return sort_passes<K, 10>(c, plan, a, b, n, ws, in_b);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+RadixPlan make_radix_plan(uint32_t k, const uint32_t* col_bits, uint32_t digit_bits) {
+  RadixPlan pl;
+  pl.k = k;
+  pl.bits = (digit_bits == 10) ? 10 : 8;
+  uint32_t pos[kMaxK] = {0, 0, 0, 0};
+  uint32_t total = 0;
+  for (int c = (int)k - 1; c >= 0; --c) {
+    pos[c] = total;
+    total += col_bits[c];
+  }
+  pl.npass = (total + pl.bits - 1) / pl.bits;
+  for (uint32_t p = 0; p < pl.npass; ++p) {
+    RadixPlan::Pass ps{};
+    const uint32_t lo = p * pl.bits, hi = lo + pl.bits < total ? lo + pl.bits : total;
+    for (uint32_t c = 0; c < k; ++c) {
+      const uint32_t s = lo > pos[c] ? lo : pos[c];
+      const uint32_t e = hi < pos[c] + col_bits[c] ? hi : pos[c] + col_bits[c];
+      if (s < e) {
+        ps.sh[c] = s - pos[c];
+        ps.mask[c] = (e - s >= 32) ? 0xFFFFFFFFu : ((1u << (e - s)) - 1u);
+        ps.dsh[c] = s - lo;
+      }
+    }
+    pl.pass.push_back(ps);
+  }
+  return pl;
+}
+
+size_t radix_workspace(uint64_t n, uint32_t digit_bits) {
+  const uint64_t R = 1ull << (digit_bits == 10 ? 10 : 8);
+  const uint64_t ntiles = (n + kRTile - 1) / kRTile;
+  const uint64_t cells = R * ntiles;
+  return ((cells * 4 + 255) & ~uint64_t(255)) + ((cells * 8 + 255) & ~uint64_t(255)) +
+         scan_workspace(cells);
+}
+
+cudaError_t radix_sort(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t n, void* ws,
+                       bool* in_b) {
+  *in_b = false;
+  if (n <= 1 || plan.npass == 0) return cudaSuccess;
+  switch (plan.k) {
+    case 1: return sort_k<1>(c, plan, a, b, n, ws, in_b);
+    case 2: return sort_k<2>(c, plan, a, b, n, ws, in_b);
+    case 3: return sort_k<3>(c, plan, a, b, n, ws, in_b);
+    case 4: return sort_k<4>(c, plan, a, b, n, ws, in_b);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t column_max(Ctx& c, ColsIn in, uint32_t k, uint64_t n, uint32_t* d_max) {
+  cudaError_t e = cudaMemsetAsync(d_max, 0, sizeof(uint32_t) * k, c.st);
+  if (e != cudaSuccess || n == 0) return e;
+  ProfScope ps(c, kMisc, 4.0 * k * n);
+  uint64_t blocks = (n + 2047) / 2048;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_column_max<<<(unsigned)blocks, 256, 0, c.st>>>(in, k, n, d_max);
+  return cudaGetLastError();
+}
+
+}  // namespace cdl

@@ -1,0 +1,49 @@
+"""The C ABI library loads and exports every function include/cdl.h
+declares (CPU only: nothing here launches a kernel)."""
+import ctypes
+
+import pytest
+
+from paper_2501_13051_gb300 import build as B
+from paper_2501_13051_gb300 import cdl
+
+
+@pytest.fixture(scope="module")
+def libcdl():
+    B.build()
+    return cdl.lib()
+
+
+def test_header_declares_the_engine_and_step_calls():
+    names = cdl.header_functions()
+    for want in ("cdl_create", "cdl_destroy", "cdl_relation_create", "cdl_relation_load",
+                 "cdl_rule_add", "cdl_run", "cdl_relation_size", "cdl_relation_export",
+                 "cdl_last_error", "cdl_hash_build", "cdl_join_count", "cdl_exclusive_scan",
+                 "cdl_join", "cdl_sort_unique", "cdl_diff_merge"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(libcdl):
+    missing = [n for n in cdl.header_functions() if not hasattr(libcdl, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls(libcdl):
+    o = cdl.Options()
+    libcdl.cdl_options_default(ctypes.byref(o))
+    assert o.hash_load == 0.5 and o.radix_bits == 8 and o.max_iters == 0
+    # 16-byte slots, power-of-two count, load factor respected
+    for n, load in ((0, 0.5), (1, 0.5), (1000, 0.5), (1000, 0.8), (1 << 20, 0.5)):
+        b = libcdl.cdl_hash_table_bytes(n, load)
+        slots = b // 16
+        assert b % 16 == 0 and slots & (slots - 1) == 0 and slots >= max(16, n / load)
+    assert libcdl.cdl_last_error(None) == b"no engine"
+    assert libcdl.cdl_create(None, None) == -1
+
+
+def test_structs_match_header_sizes():
+    # the ctypes mirrors must keep the header's field order and widths
+    assert ctypes.sizeof(cdl.Term) == 8
+    assert ctypes.sizeof(cdl.ColRef) == 8
+    assert ctypes.sizeof(cdl.Atom) == 16
+    assert ctypes.sizeof(cdl.Stats) == 8 * 11

@@ -1,0 +1,134 @@
+"""Whole-fixpoint parity of the GPU engine with the CPU oracle, through the
+C ABI: the same sorted tuple sets, the same iteration counts and the same
+per-round delta sizes on the same seeded inputs; plus the engine's error
+paths (reserved value, round limit, rule shape, call order)."""
+import numpy as np
+import pytest
+
+from paper_2501_13051_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cdl():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a GPU"
+    from paper_2501_13051_gb300 import build as B
+    B.build()
+    from paper_2501_13051_gb300 import cdl as C
+    return C
+
+
+def check(cdl, oracle_lib, prog, **opts):
+    got, st = cdl.run_program(prog, **opts)
+    want = oracle_lib.run_program(prog)
+    for nm in prog.arity:
+        assert np.array_equal(got[nm], want.relations[nm]), nm
+    assert st.iterations == want.iterations
+    assert st.rounds == want.rounds
+    per_round = [sum(want.deltas[nm][k] for nm in prog.idb()) for k in range(want.rounds)]
+    assert st.delta_per_round == per_round
+    assert st.derived_tuples == want.derived(prog)
+    return st
+
+
+@pytest.mark.parametrize("n,m,seed", [(1000, 1500, 1), (1000, 1500, 11), (50, 120, 2), (400, 380, 3)])
+def test_transitive_closure(cdl, oracle_lib, n, m, seed):
+    check(cdl, oracle_lib, W.tc_program(W.er_graph(n, m, seed)))
+
+
+@pytest.mark.parametrize("n,seed", [(2000, 2), (5000, 11)])
+@pytest.mark.parametrize("make", [W.sg_program, W.sg_paper_program])
+def test_same_generation(cdl, oracle_lib, n, seed, make):
+    check(cdl, oracle_lib, make(W.random_forest(n, seed)))
+
+
+def test_points_to_scaled(cdl, oracle_lib):
+    check(cdl, oracle_lib, W.points_to_program(W.points_to_edb(1 / 2048, 3)))
+
+
+def test_owl_scaled(cdl, oracle_lib):
+    check(cdl, oracle_lib, W.owl_program(*W.owl_triples(200_000, 4, n_entities=50_000)))
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_programs(cdl, oracle_lib, seed):
+    check(cdl, oracle_lib, W.random_program(seed))
+
+
+@pytest.mark.parametrize("opts", [dict(radix_bits=10), dict(hash_load=0.8), dict(timing=True)])
+def test_engine_options_do_not_change_results(cdl, oracle_lib, opts):
+    check(cdl, oracle_lib, W.sg_program(W.random_forest(1500, 5)), **opts)
+
+
+def test_device_load_and_export(cdl, oracle_lib):
+    import torch
+    e = W.er_graph(200, 300, 7)
+    prog = W.tc_program(e)
+    with cdl.Engine() as eng:
+        eng.relation("edge", 2)
+        eng.relation("path", 2)
+        cols = [torch.from_numpy(np.ascontiguousarray(e[:, k]).view(np.int32)).cuda() for k in range(2)]
+        eng.load("edge", cols)
+        for r in prog.rules:
+            eng.rule(r.head, r.body, r.neq)
+        eng.run()
+        dcols = eng.export("path", device=True)
+        got = np.stack([c.cpu().numpy().view(np.uint32) for c in dcols], axis=1)
+    want = oracle_lib.run_program(prog)
+    assert np.array_equal(got, want.relations["path"])
+
+
+def test_load_deduplicates_and_merges(cdl):
+    with cdl.Engine() as eng:
+        eng.relation("r", 2)
+        eng.load("r", np.array([[3, 1], [1, 2], [3, 1]], np.uint32))
+        eng.load("r", np.array([[1, 2], [0, 9]], np.uint32))
+        assert eng.export("r").tolist() == [[0, 9], [1, 2], [3, 1]]
+
+
+def test_reserved_value_rejected(cdl):
+    with cdl.Engine() as eng:
+        eng.relation("r", 1)
+        with pytest.raises(cdl.CdlError) as ei:
+            eng.load("r", np.array([[5], [0xFFFFFFFF]], np.uint32))
+        assert ei.value.name == "CDL_E_VALUE"
+        eng.load("r", np.array([[5]], np.uint32))  # the engine stays usable
+        assert eng.size("r") == 1
+
+
+def test_max_iters(cdl):
+    prog = W.tc_program(W.er_graph(100, 200, 1))
+    with pytest.raises(cdl.CdlError) as ei:
+        cdl.run_program(prog, max_iters=2)
+    assert ei.value.name == "CDL_E_MAXITER"
+
+
+def test_rule_and_state_errors(cdl):
+    with cdl.Engine() as eng:
+        eng.relation("a", 2)
+        eng.relation("b", 2)
+        with pytest.raises(cdl.CdlError):  # head variable not bound in the body
+            eng.rule(("b", ("x", "q")), [("a", ("x", "y"))])
+        with pytest.raises(cdl.CdlError):  # arity mismatch
+            eng.rule(("b", ("x",)), [("a", ("x", "y"))])
+        eng.rule(("b", ("x", "y")), [("a", ("x", "y"))])
+        eng.run()
+        with pytest.raises(cdl.CdlError) as ei:
+            eng.rule(("b", ("x", "y")), [("a", ("x", "y"))])
+        assert ei.value.name == "CDL_E_STATE"
+        with pytest.raises(cdl.CdlError):
+            eng.run()
+
+
+def test_export_capacity(cdl):
+    import ctypes
+    with cdl.Engine() as eng:
+        eng.relation("r", 1)
+        eng.load("r", np.arange(10, dtype=np.uint32).reshape(-1, 1))
+        buf = np.zeros(4, np.uint32)
+        got = ctypes.c_uint64()
+        st = cdl.lib().cdl_relation_export(eng._h, eng.rels["r"], cdl._ptrs([buf.ctypes.data]), 4,
+                                           ctypes.byref(got), 0)
+        assert st == -3 and got.value == 10
