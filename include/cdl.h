@@ -203,6 +203,22 @@ cdl_status cdl_join_count(const uint32_t* probe, uint64_t n, const void* table,
 cdl_status cdl_exclusive_scan(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* total_host,
                               void* workspace, size_t* ws_bytes, void* stream);
 
+/* The same scan as cdl_exclusive_scan for callers that cannot allocate
+ * device memory (no cudaMalloc, no workspace to hand over): it allocates
+ * nothing.  The paper has no counterpart; this is a convenience of this
+ * library.  Its scratch is a fixed array inside the library, 512 KiB + 8
+ * bytes on every GPU where the library is loaded, held until the process
+ * exits; so n may not exceed 134,217,728 (65,536 tiles of 2048), and larger
+ * n gives CDL_E_CAPACITY with nothing launched.  The first call on each GPU
+ * looks up the array's device address (with that GPU current); make that
+ * first call before any stream capture.  All calls share the one array:
+ * calls whose kernels overlap on the GPU (other streams, other threads)
+ * race on it and must be serialised by the caller.  Every value the scan
+ * reads from the array is written by the same call first.  Arguments and
+ * results as for cdl_exclusive_scan. */
+cdl_status cdl_exclusive_scan_noalloc(const uint32_t* in, uint64_t n, uint64_t* out,
+                                      uint64_t* total_host, void* stream);
+
 /* Where a head column of a join takes its value from. */
 typedef struct {
   uint32_t side; /* 0: probe row column, 1: build row column, 2: constant */

@@ -110,6 +110,7 @@ def lib():
         "cdl_hash_build": (ctypes.c_int, [VP, U64, VP, U64, VP]),
         "cdl_join_count": (ctypes.c_int, [VP, U64, VP, U64, VP, VP]),
         "cdl_exclusive_scan": (ctypes.c_int, [VP, U64, VP, P(U64), VP, P(ctypes.c_size_t), VP]),
+        "cdl_exclusive_scan_noalloc": (ctypes.c_int, [VP, U64, VP, P(U64), VP]),
         "cdl_join": (ctypes.c_int, [PP, U32, U64, U32, PP, U32, U64, U32, P(ColRef), U32,
                                     P(ColRef), U32, PP, U64, P(U64), VP, P(ctypes.c_size_t), VP]),
         "cdl_sort_unique": (ctypes.c_int, [PP, U32, U64, PP, P(U64), VP, P(ctypes.c_size_t), VP]),
