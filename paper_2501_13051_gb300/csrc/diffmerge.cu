@@ -1,0 +1,343 @@
+// Step (d): set difference + eager merge (Section 4, "Union and
+// Deduplication": delta = New - Full by the difference operator; Section 3,
+// "Continuous Memory Layout": delta merged at once into one contiguous,
+// sorted Full).  Both inputs are sorted; Full is unique, New may repeat.  In
+// the merged order a Full tuple precedes an equal New tuple, so a New tuple
+// is a repeat exactly when it equals the Full tuple or the New tuple just
+// before it in that order: the removal of repeats (step c's "unique") is
+// folded into this step.
+//
+// The combined sequence is cut into tiles of 4096 items by merge-path splits
+// (Green, McColl & Bader, "GPU merge path", ICS 2012), computed for all
+// tiles at once by a small kernel with one thread per split.  Then:
+//   count  -- per tile, every New tuple finds its co-rank in the tile's Full
+//             slice (how many of its Full tuples are <= it) by binary
+//             search, which also tells whether it repeats a Full tuple; a
+//             tile with many New tuples first stages its Full slice in
+//             shared memory, a sparse one searches with cached global loads
+//             and touches few Full sectors.  The co-rank of every New tuple
+//             (or a repeat mark) and the tile's count of new tuples are
+//             stored;
+//   scan   -- exclusive scan of the tile counts: each tile's delta offset
+//             and |delta|;
+//   write  -- per tile, a block scan ranks its new tuples, a histogram of
+//             their co-ranks scanned over the Full slice gives every Full
+//             tuple its shift (the new tuples placed before it), and the
+//             Full slice streams from global memory through registers to its
+//             shifted place; the new tuples go to delta at the tile's offset
+//             and into the merged relation at co-rank + rank.
+// No block waits on another.  Full and New are read once by the write pass
+// and the merged Full and delta written once; the count pass adds New, the
+// co-ranks, and the Full slices of dense tiles.
+#include "kernels.h"
+
+namespace cdl {
+
+namespace {
+
+constexpr int kDT = 256;
+constexpr int kDItems = 16;
+constexpr int kDTile = kDT * kDItems;  // merged items per tile
+constexpr uint32_t kRepeat = 0xFFFFFFFFu;
+
+template <int K>
+__device__ __forceinline__ bool g_le(const ColsIn& a, uint64_t i, const ColsIn& b, uint64_t j) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t x = __ldg(a.c[k] + i), y = __ldg(b.c[k] + j);
+    if (x != y) return x < y;
+  }
+  return true;
+}
+
+// Number of Full tuples among the first d of the merged order.
+template <int K>
+__device__ __forceinline__ uint64_t merge_split(const ColsIn& F, uint64_t nF, const ColsIn& U,
+                                                uint64_t nU, uint64_t d) {
+  uint64_t lo = d > nU ? d - nU : 0, hi = d < nF ? d : nF;
+  while (lo < hi) {
+    const uint64_t mid = lo + ((hi - lo) >> 1);
+    if (g_le<K>(F, mid, U, d - mid - 1))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <int K>
+__global__ void k_merge_splits(ColsIn F, uint64_t nF, ColsIn U, uint64_t nU,
+                               uint64_t* __restrict__ splits, uint64_t ntiles) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > ntiles) return;
+  const uint64_t d = t * kDTile < nF + nU ? t * kDTile : nF + nU;
+  splits[t] = merge_split<K>(F, nF, U, nU, d);
+}
+
+template <int K>
+__device__ __forceinline__ bool eq_at(const ColsIn& a, uint64_t i, const uint32_t (&t)[K]) {
+  bool e = true;
+#pragma unroll
+  for (int k = 0; k < K; ++k) e &= __ldg(a.c[k] + i) == t[k];
+  return e;
+}
+
+// Number of tuples <= t among s[0..n) (column k of item i at s[k*kDTile + i]).
+template <int K>
+__device__ __forceinline__ uint32_t count_le_smem(const uint32_t* s, uint32_t n,
+                                                  const uint32_t (&t)[K]) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    bool le = true;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint32_t x = s[k * kDTile + mid];
+      if (x != t[k]) {
+        le = x < t[k];
+        break;
+      }
+    }
+    if (le)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Number of tuples <= t among F[lo..hi), as an index into F.
+template <int K>
+__device__ __forceinline__ uint64_t count_le_global(const ColsIn& F, uint64_t lo, uint64_t hi,
+                                                    const uint32_t (&t)[K]) {
+  while (lo < hi) {
+    const uint64_t mid = lo + ((hi - lo) >> 1);
+    bool le = true;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint32_t x = __ldg(F.c[k] + mid);
+      if (x != t[k]) {
+        le = x < t[k];
+        break;
+      }
+    }
+    if (le)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t nF, uint64_t nU,
+                                                   const uint64_t* __restrict__ splits,
+                                                   uint32_t* __restrict__ corank,
+                                                   uint32_t* __restrict__ tile_cnt) {
+  extern __shared__ uint32_t s[];  // K x kDTile: the Full slice of a dense tile
+  __shared__ uint32_t red[kDT / 32 + 1];
+  const uint64_t tile = blockIdx.x;
+  const uint64_t d0 = tile * kDTile;
+  const uint64_t d1 = d0 + kDTile < nF + nU ? d0 + kDTile : nF + nU;
+  const uint64_t a0 = splits[tile], a1 = splits[tile + 1];
+  const uint64_t b0 = d0 - a0, b1 = d1 - a1;
+  const uint32_t na = (uint32_t)(a1 - a0), nb = (uint32_t)(b1 - b0);
+  const bool dense = (uint64_t)nb * 16 >= na;
+  if (dense) {
+    for (uint32_t i = threadIdx.x; i < na; i += kDT) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) s[k * kDTile + i] = __ldg(F.c[k] + a0 + i);
+    }
+    __syncthreads();
+  }
+  uint32_t cnt = 0;
+  for (uint64_t j = b0 + threadIdx.x; j < b1; j += kDT) {
+    uint32_t v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = __ldg(U.c[k] + j);
+    bool rep = j > 0 && eq_at<K>(U, j - 1, v);
+    uint32_t p = 0;
+    if (!rep) {
+      // the Full tuple just before v in merged order is F[a0 + p - 1]
+      p = dense ? count_le_smem<K>(s, na, v) : (uint32_t)(count_le_global<K>(F, a0, a1, v) - a0);
+      if (p > 0) {
+        if (dense) {
+          bool e = true;
+#pragma unroll
+          for (int k = 0; k < K; ++k) e &= s[k * kDTile + p - 1] == v[k];
+          rep = e;
+        } else {
+          rep = eq_at<K>(F, a0 + p - 1, v);
+        }
+      } else {
+        rep = a0 > 0 && eq_at<K>(F, a0 - 1, v);
+      }
+    }
+    corank[j] = rep ? kRepeat : p;
+    cnt += rep ? 0u : 1u;
+  }
+  uint32_t tot;
+  block_exclusive_sum<kDT, uint32_t>(cnt, red, &tot);
+  if (threadIdx.x == 0) tile_cnt[tile] = tot;
+}
+
+// shift table index with one padding word per 32 (blocked scans stay
+// free of bank conflicts)
+__device__ __forceinline__ uint32_t pad(uint32_t i) { return i + (i >> 5); }
+constexpr int kShiftWords = kDTile + 1 + (kDTile + 1) / 32 + 1;
+
+template <int K>
+__global__ void __launch_bounds__(kDT) k_merge_write(ColsIn F, uint64_t nF, ColsIn U, uint64_t nU,
+                                                     const uint64_t* __restrict__ splits,
+                                                     const uint32_t* __restrict__ corank,
+                                                     const uint64_t* __restrict__ tile_pre,
+                                                     ColsOut D, ColsOut M) {
+  __shared__ uint32_t shift[kShiftWords];
+  __shared__ uint32_t red[kDT / 32 + 1];
+  const uint64_t tile = blockIdx.x;
+  const uint64_t d0 = tile * kDTile;
+  const uint64_t d1 = d0 + kDTile < nF + nU ? d0 + kDTile : nF + nU;
+  const uint64_t a0 = splits[tile], a1 = splits[tile + 1];
+  const uint64_t b0 = d0 - a0, b1 = d1 - a1;
+  const uint32_t na = (uint32_t)(a1 - a0), nb = (uint32_t)(b1 - b0);
+  const uint64_t dpre = tile_pre[tile];
+  const uint64_t mbase = a0 + dpre;
+  const bool merged = M.c[0] != nullptr;
+  uint32_t tot_new = 0;
+  if (nb) {
+    // New tuples, blocked: thread owns [j0, j1) so that ranks follow order
+    const uint32_t m = (nb + kDT - 1) / kDT;
+    const uint32_t j0 = threadIdx.x * m < nb ? threadIdx.x * m : nb;
+    const uint32_t j1 = j0 + m < nb ? j0 + m : nb;
+    uint32_t p[kDItems];
+    uint32_t newmask = 0;
+#pragma unroll
+    for (int q = 0; q < kDItems; ++q) {
+      p[q] = kRepeat;
+      if (j0 + q < j1) p[q] = __ldg(corank + b0 + j0 + q);
+      if (p[q] != kRepeat) newmask |= 1u << q;
+    }
+    const uint32_t rank0 = block_exclusive_sum<kDT, uint32_t>(__popc(newmask), red, &tot_new);
+    if (tot_new && merged) {
+      for (uint32_t i = threadIdx.x; i <= na; i += kDT) shift[pad(i)] = 0;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < kDItems; ++q)
+        if ((newmask >> q) & 1u) atomicAdd(&shift[pad(p[q])], 1u);
+      __syncthreads();
+      const uint32_t c0 = threadIdx.x * kDItems;  // blocked inclusive scan over [0, na]
+      uint32_t run = 0;
+#pragma unroll
+      for (int q = 0; q < kDItems; ++q) run += c0 + q <= na ? shift[pad(c0 + q)] : 0u;
+      uint32_t tot;
+      uint32_t acc = block_exclusive_sum<kDT, uint32_t>(run, red, &tot);
+#pragma unroll
+      for (int q = 0; q < kDItems; ++q)
+        if (c0 + q <= na) {
+          acc += shift[pad(c0 + q)];
+          shift[pad(c0 + q)] = acc;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kDItems; ++q) {
+      if ((newmask >> q) & 1u) {
+        const uint32_t r = rank0 + __popc(newmask & ((1u << q) - 1u));
+        const uint64_t j = b0 + j0 + q;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const uint32_t v = __ldg(U.c[k] + j);
+          D.c[k][dpre + r] = v;
+          if (merged) M.c[k][mbase + p[q] + r] = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!merged) return;
+  // the Full slice, four loads in flight per thread and column
+  constexpr int kU = 4;
+  for (uint32_t base = 0; base < na; base += kU * kDT) {
+    uint32_t v[kU][K];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint32_t i = base + u * kDT + threadIdx.x;
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[u][k] = i < na ? __ldg(F.c[k] + a0 + i) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint32_t i = base + u * kDT + threadIdx.x;
+      if (i < na) {
+        const uint64_t at = mbase + i + (tot_new ? shift[pad(i)] : 0u);
+#pragma unroll
+        for (int k = 0; k < K; ++k) M.c[k][at] = v[u][k];
+      }
+    }
+  }
+}
+
+uint64_t dm_tiles(uint64_t n_full, uint64_t n_fresh) {
+  return (n_full + n_fresh + kDTile - 1) / kDTile;
+}
+
+size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
+
+template <int K>
+cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, uint64_t n_fresh,
+                           ColsOut delta, ColsOut merged, uint64_t* d_ndelta, void* ws) {
+  const uint64_t tiles = dm_tiles(n_full, n_fresh);
+  char* w = static_cast<char*>(ws);
+  uint64_t* splits = reinterpret_cast<uint64_t*>(w);
+  w += up256((tiles + 1) * 8);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(w);
+  w += up256(tiles * 4);
+  uint64_t* pre = reinterpret_cast<uint64_t*>(w);
+  w += up256(tiles * 8);
+  uint32_t* corank = reinterpret_cast<uint32_t*>(w);
+  w += up256((n_fresh ? n_fresh : 1) * 4);
+  void* scan_ws = w;
+  const size_t smem_count = sizeof(uint32_t) * K * kDTile;
+  cudaError_t e = cudaFuncSetAttribute(k_count_new<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_count);
+  if (e != cudaSuccess) return e;
+  {
+    // New read, co-ranks written; Full sectors are read only where touched
+    ProfScope p(c, kDiffCount, (4.0 * K + 4.0) * n_fresh);
+    k_merge_splits<K><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, c.st>>>(full, n_full, fresh,
+                                                                             n_fresh, splits, tiles);
+    k_count_new<K><<<(unsigned)tiles, kDT, smem_count, c.st>>>(full, fresh, n_full, n_fresh, splits,
+                                                               corank, cnt);
+  }
+  e = exclusive_scan(c, cnt, tiles, pre, d_ndelta, scan_ws);
+  if (e != cudaSuccess) return e;
+  // read Full, New and the co-ranks, write Full again; the delta part of the
+  // writes (merged and delta) is added once its size is known
+  const double mb = merged.c[0] ? 4.0 * K * n_full : 0.0;
+  ProfScope p(c, kDiffMerge, 4.0 * K * (n_full + n_fresh) + 4.0 * n_fresh + mb);
+  k_merge_write<K><<<(unsigned)tiles, kDT, 0, c.st>>>(full, n_full, fresh, n_fresh, splits, corank,
+                                                      pre, delta, merged);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t diff_merge_workspace(uint64_t n_full, uint64_t n_fresh) {
+  const uint64_t tiles = dm_tiles(n_full, n_fresh);
+  return up256((tiles + 1) * 8) + up256(tiles * 4) + up256(tiles * 8) +
+         up256((n_fresh ? n_fresh : 1) * 4) + scan_workspace(tiles);
+}
+
+cudaError_t diff_merge(Ctx& c, uint32_t k, ColsIn full, uint64_t n_full, ColsIn fresh,
+                       uint64_t n_fresh, ColsOut delta, ColsOut merged, uint64_t* d_ndelta,
+                       void* ws) {
+  if (n_full + n_fresh == 0) return cudaMemsetAsync(d_ndelta, 0, sizeof(uint64_t), c.st);
+  switch (k) {
+    case 1: return run_diff_merge<1>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws);
+    case 2: return run_diff_merge<2>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws);
+    case 3: return run_diff_merge<3>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws);
+    case 4: return run_diff_merge<4>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace cdl

@@ -812,6 +812,10 @@ struct cdl_engine {
       ++joins;
       if (total == 0) return CDL_OK;
       const bool filter = js.n_neq > 0 || js.n_eq > 0;
+      ws.reset();
+      const size_t wws = join_write_workspace(P.n, total);
+      DBuf wsp = alloc(wws);
+      if (!wsp.p) return fail(CDL_E_NOMEM, "join splits");
       if (last) {
         Relation& H = *rels[rule.head.rel];
         H.fresh_ub = h_ctl[kSlotCursor + rule.head.rel];
@@ -819,7 +823,7 @@ struct cdl_engine {
         r = ensure_fresh(H, total);
         if (r != CDL_OK) return r;
         e = join_write(ctx, js, static_cast<const uint64_t*>(off.p), total, H.fresh.out(), base,
-                       dslot(kSlotCursor + rule.head.rel), H.fresh.cap);
+                       dslot(kSlotCursor + rule.head.rel), H.fresh.cap, wsp.p, wws);
         if (e != cudaSuccess) return cuda_fail(e, "join write");
         return CDL_OK;
       }
@@ -829,7 +833,7 @@ struct cdl_engine {
       e = cudaMemsetAsync(dslot(kSlotAux), 0, 8, st);
       if (e == cudaSuccess)
         e = join_write(ctx, js, static_cast<const uint64_t*>(off.p), total, next.owned.out(), 0,
-                       dslot(kSlotAux), total);
+                       dslot(kSlotAux), total, wsp.p, wws);
       if (e != cudaSuccess) return cuda_fail(e, "join write");
       if (filter) {
         r = fetch(kSlotAux, 1);

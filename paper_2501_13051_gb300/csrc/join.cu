@@ -89,6 +89,16 @@ __device__ __forceinline__ uint64_t merge_split(const uint64_t* off, uint64_t n,
   return lo;
 }
 
+// All blocks' splits at once, one thread per split, so that no block
+// waits on a chain of dependent global loads before its first useful one.
+__global__ void k_write_splits(const uint64_t* __restrict__ off, uint64_t n, uint64_t total,
+                               uint64_t* __restrict__ splits, uint64_t nblocks) {
+  const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > nblocks) return;
+  const uint64_t d = b * kJTile < n + total ? b * kJTile : n + total;
+  splits[b] = merge_split(off, n, total, d);
+}
+
 __device__ __forceinline__ uint32_t ref_value(const JoinSpec& j, const Ref& r, uint64_t row,
                                               uint64_t brow) {
   if (r.side == 0) return __ldg(j.probe.c[r.v] + row);
@@ -100,6 +110,7 @@ template <bool FILTER>
 __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint64_t* __restrict__ off,
                                                     uint64_t total, ColsOut out, uint64_t base,
                                                     unsigned long long* cursor, uint64_t out_cap,
+                                                    const uint64_t* __restrict__ splits,
                                                     uint32_t* err) {
   __shared__ uint64_t s_off[kJTile + 1];
   __shared__ uint32_t s_start[kJTile + 1];
@@ -109,8 +120,12 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
   const uint64_t nm = j.n_probe + total;
   const uint64_t d0 = (uint64_t)blockIdx.x * kJTile;
   const uint64_t d1 = d0 + kJTile < nm ? d0 + kJTile : nm;
-  if (threadIdx.x == 0) s_split[0] = merge_split(off, j.n_probe, total, d0);
-  if (threadIdx.x == 32) s_split[1] = merge_split(off, j.n_probe, total, d1);
+  if (splits) {
+    if (threadIdx.x < 2) s_split[threadIdx.x] = splits[blockIdx.x + threadIdx.x];
+  } else {
+    if (threadIdx.x == 0) s_split[0] = merge_split(off, j.n_probe, total, d0);
+    if (threadIdx.x == 32) s_split[1] = merge_split(off, j.n_probe, total, d1);
+  }
   if (!FILTER && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(cursor, (unsigned long long)total);
   __syncthreads();
   const uint64_t j0 = s_split[0], j1 = s_split[1];
@@ -205,13 +220,24 @@ cudaError_t join_count_scan(Ctx& c, const JoinSpec& j, uint64_t* d_off, uint64_t
   return scan_finish(c, counts, j.n_probe, d_off, d_total, scan_ws);
 }
 
+size_t join_write_workspace(uint64_t n_probe, uint64_t total) {
+  const uint64_t blocks = (n_probe + total + kJTile - 1) / kJTile;
+  return ((blocks + 1) * 8 + 255) & ~uint64_t(255);
+}
+
 cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_t total,
-                       ColsOut out, uint64_t base, uint64_t* d_cursor, uint64_t out_cap) {
+                       ColsOut out, uint64_t base, uint64_t* d_cursor, uint64_t out_cap,
+                       void* ws, size_t ws_bytes) {
   if (total == 0 || j.n_probe == 0) return cudaSuccess;
   const uint64_t nm = j.n_probe + total;
   const uint64_t blocks = (nm + kJTile - 1) / kJTile;
   const bool filter = j.n_neq > 0 || j.n_eq > 0;
-  // offsets + re-probe per row, build gather per build column read, head write
+  uint64_t* splits = nullptr;
+  if (ws && ws_bytes >= join_write_workspace(j.n_probe, total)) {
+    splits = static_cast<uint64_t*>(ws);
+    k_write_splits<<<(unsigned)((blocks + 1 + 255) / 256), 256, 0, c.st>>>(d_off, j.n_probe, total,
+                                                                          splits, blocks);
+  }
   // per probe row: two offsets, key, re-probed slot, its own head columns;
   // per output: the gathered build columns and the written head columns
   uint32_t nbuild = 0, nprobe = 0;
@@ -225,10 +251,10 @@ cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_
   auto* cur = reinterpret_cast<unsigned long long*>(d_cursor);
   if (filter)
     k_join_write<true><<<(unsigned)blocks, kJT, 0, c.st>>>(j, d_off, total, out, base, cur, out_cap,
-                                                          c.d_err);
+                                                          splits, c.d_err);
   else
     k_join_write<false><<<(unsigned)blocks, kJT, 0, c.st>>>(j, d_off, total, out, base, cur,
-                                                           out_cap, c.d_err);
+                                                           out_cap, splits, c.d_err);
   return cudaGetLastError();
 }
 

@@ -121,8 +121,12 @@ cudaError_t join_count_scan(Ctx& c, const JoinSpec& j, uint64_t* d_off, uint64_t
 // Pass 3: writes the output tuples.  With no filters, tuple o goes to
 // out[base + o] and *d_cursor grows by total; with filters, survivors are
 // packed at *d_cursor (atomic).  out_cap bounds every write.
+// ws (optional, join_write_workspace bytes) holds every block's merge-path
+// split, computed up front; without it each block searches for its own.
+size_t join_write_workspace(uint64_t n_probe, uint64_t total);
 cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_t total,
-                       ColsOut out, uint64_t base, uint64_t* d_cursor, uint64_t out_cap);
+                       ColsOut out, uint64_t base, uint64_t* d_cursor, uint64_t out_cap,
+                       void* ws, size_t ws_bytes);
 
 // -------------------------------------------------------------------- sort
 // Digit plan of an LSD radix sort over the packed key of K columns.

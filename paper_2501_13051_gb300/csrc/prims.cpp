@@ -178,7 +178,8 @@ cdl_status cdl_join(const uint32_t* const* probe_cols, uint32_t probe_arity, uin
   if (out_cap < total) return CDL_E_CAPACITY;
   ColsOut out;
   for (uint32_t k = 0; k < CDL_MAX_ARITY; ++k) out.c[k] = k < out_arity ? out_cols[k] : nullptr;
-  e = join_write(c, j, off, total, out, 0, head + 2, out_cap);
+  // the count workspace is free again: it holds the write splits if large enough
+  e = join_write(c, j, off, total, out, 0, head + 2, out_cap, cws, join_count_workspace(n_probe));
   if (e != cudaSuccess) return CDL_E_CUDA;
   s = read_flags(head, c.st, h, 3);
   if (s != CDL_OK) return s;
