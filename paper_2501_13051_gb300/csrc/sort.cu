@@ -18,8 +18,8 @@ namespace cdl {
 
 namespace {
 
-constexpr int kRT = 256;
-constexpr int kRItems = 16;
+constexpr int kRT = 512;
+constexpr int kRItems = 8;
 constexpr int kRTile = kRT * kRItems;
 constexpr int kRW = kRT / 32;
 
@@ -44,15 +44,17 @@ __global__ void __launch_bounds__(kRT) k_radix_upsweep(ColsIn in, uint64_t n, Pa
   for (int i = threadIdx.x; i < R; i += kRT) h[i] = 0;
   __syncthreads();
   const uint64_t base = (uint64_t)blockIdx.x * kRTile;
-#pragma unroll 4
+  uint32_t v[kRItems][K];
+#pragma unroll
+  for (int it = 0; it < kRItems; ++it) {  // every load in flight before the first use
+    const uint64_t idx = base + (uint64_t)it * kRT + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[it][k] = (idx < n && p.mask[k]) ? __ldg(in.c[k] + idx) : 0u;
+  }
+#pragma unroll
   for (int it = 0; it < kRItems; ++it) {
     const uint64_t idx = base + (uint64_t)it * kRT + threadIdx.x;
-    if (idx < n) {
-      uint32_t v[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) v[k] = p.mask[k] ? __ldg(in.c[k] + idx) : 0u;
-      atomicAdd(&h[digit_of<K>(v, p)], 1u);
-    }
+    if (idx < n) atomicAdd(&h[digit_of<K>(v[it], p)], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < R; i += kRT) tile_hist[(uint64_t)i * ntiles + blockIdx.x] = h[i];
