@@ -2,21 +2,25 @@
 """Benchmark of the semi-naive Datalog fixpoint on GB300.
 
 One step = one complete fixpoint (every round: hash index, three-pass join,
-radix sort + dedup, difference + merge) of the same-generation program on a
-seeded random forest of 200,000 nodes (each node's parent uniform among the
-earlier nodes with probability 0.98, else a root) plus 2% random cross
-edges, with the input edge columns already resident in device memory.
-Metric: derived tuples per second (sum of the derived relation's size over
-the steps / device time of the steps).
+radix sort + dedup, difference + merge) of a workload whose input columns
+are already resident in device memory.  The default workload is
+same-generation on a seeded random forest of 200,000 nodes (each node's
+parent uniform among the earlier nodes with probability 0.98, else a root)
+plus 2% random cross edges.  Metric: derived tuples per second (the derived
+relations' sizes summed over the steps / device time of the steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload NAME] [--scale S]
+
+Workloads: sg-forest-200k (default), tc-er-1000-1500, points-to (scale S of
+2M variables / 4M assign / 1M dereference, Zipf 1.1), owl-rl-20m.
 
 Under torchrun each rank runs an independent instance (seed + rank): the
 fixpoint has no exchange step here, so ranks are replicas and the value is
 the tuples all ranks derived / the slowest rank's time.
 
 Also reported: an end-to-end figure through the C ABI with host buffers
-(edge upload and export of the whole derived relation inside the timed
+(input upload and export of every derived relation inside the timed
 region), the roofline of the dominant kernel (its algorithmic bytes / its
 CUDA-event time over the timed steps, against the measured HBM copy
 bandwidth), and the CPU oracle timed on a bounded sample of the same
@@ -45,21 +49,46 @@ from paper_2501_13051_gb300 import workloads as W  # noqa: E402
 WORKLOADS = {
     "sg-forest-200k": dict(kind="sg", n=200_000, seed=2,
                            desc="same-generation on a random forest, 200000 nodes, "
-                                "p_parent 0.98, +2% cross edges"),
+                                "p_parent 0.98, +2% cross edges",
+                           sample=dict(kind="sg", n=10_000, seed=2)),
     "tc-er-1000-1500": dict(kind="tc", n=1000, m=1500, seed=1,
                             desc="transitive closure on a directed Erdos-Renyi graph, "
-                                 "1000 nodes, 1500 edges"),
+                                 "1000 nodes, 1500 edges",
+                            sample=dict(kind="tc", n=1000, m=1500, seed=1)),
+    "points-to": dict(kind="pt", scale=1 / 32, seed=3,
+                      desc="points-to analysis (valueFlow / memoryAlias / valueAlias), "
+                           "Zipf(1.1) endpoints, 2M vars / 4M assign / 1M deref times scale",
+                      sample=dict(kind="pt", scale=1 / 1024, seed=3)),
+    "owl-rl-20m": dict(kind="owl", triples=20_000_000, seed=4,
+                       desc="OWL-2-RL-style rules over 20M synthetic triples, 5M entities, "
+                            "500 classes, 200 properties, 193 rule instances",
+                       sample=dict(kind="owl", triples=1_000_000, seed=4)),
 }
-# bounded sample of the default workload for the CPU oracle (seconds of work)
-ORACLE_SAMPLE = dict(kind="sg", n=10_000, seed=2)
 METRIC = "derived tuples/s per fixpoint"
 
 
-def make_program(spec, seed_offset=0):
+def make_program(spec, seed_offset=0, scale=None):
     seed = spec["seed"] + seed_offset
-    if spec["kind"] == "sg":
+    kind = spec["kind"]
+    if kind == "sg":
         return W.sg_program(W.random_forest(spec["n"], seed))
-    return W.tc_program(W.er_graph(spec["n"], spec["m"], seed))
+    if kind == "tc":
+        return W.tc_program(W.er_graph(spec["n"], spec["m"], seed))
+    if kind == "pt":
+        return W.points_to_program(W.points_to_edb(scale or spec["scale"], seed))
+    if kind == "owl":
+        t = spec["triples"]
+        f = t / 20_000_000
+        return W.owl_program(*W.owl_triples(t, seed, n_entities=max(1000, int(5_000_000 * f))))
+    raise ValueError(kind)
+
+
+def describe_sample(spec, derived, secs):
+    what = {"sg": lambda s: f"same-generation, forest {s['n']} nodes (+2% cross edges)",
+            "tc": lambda s: f"transitive closure, ER {s['n']} nodes / {s['m']} edges",
+            "pt": lambda s: f"points-to at scale {s['scale']:g}",
+            "owl": lambda s: f"OWL-RL rules over {s['triples']} triples"}[spec["kind"]](spec)
+    return f"{what}, seed {spec['seed']}: {derived} tuples in {secs:.2f} s"
 
 
 def measured_peak():
@@ -72,8 +101,8 @@ def measured_peak():
 
 
 def kernel_traffic(name):
-    """DRAM bytes per unit for a kernel from the committed ncu summary, or
-    None when the kernel's source changed since the counters were taken."""
+    """DRAM bytes per algorithmic byte for a kernel class from the committed
+    ncu summary, or None when its source changed since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))[name]
@@ -150,7 +179,7 @@ def bench_reference(args, rank, world):
     workload per step, on this host's cores (rank 0 only)."""
     if rank != 0:
         return
-    spec = ORACLE_SAMPLE
+    spec = WORKLOADS[args.workload]["sample"]
     for _ in range(args.warmup):
         run_oracle_sample(spec)
     derived, secs = 0, 0.0
@@ -159,8 +188,7 @@ def bench_reference(args, rank, world):
         derived += d
         secs += dt
     v = derived / secs
-    sample = (f"same-generation, forest {spec['n']} nodes (+2% cross edges), seed {spec['seed']}: "
-              f"{derived // max(args.steps, 1)} tuples per step")
+    sample = describe_sample(spec, derived // max(args.steps, 1), secs / max(args.steps, 1))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "tuples/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -168,7 +196,7 @@ def bench_reference(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": args.workload, "sample": sample},
         "cpu_baseline": {"value": v, "unit": "tuples/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample + ", 1 thread"},
         "e2e": {"value": v, "unit": "tuples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -180,20 +208,29 @@ def bench_gb300(args, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     spec = WORKLOADS[args.workload]
-    prog = make_program(spec, seed_offset=rank)
-    edges = prog.edb["edge"]
-    head = "sg" if spec["kind"] == "sg" else "path"
-    dev_cols = [torch.from_numpy(np.ascontiguousarray(edges[:, k]).view(np.int32)).cuda()
-                for k in range(2)]
+    prog = make_program(spec, seed_offset=rank, scale=args.scale)
+    idb = prog.idb()
+    host_cols = {nm: [np.ascontiguousarray(rows[:, k]) for k in range(prog.arity[nm])]
+                 for nm, rows in prog.edb.items()}
+    dev_edb = {nm: [torch.from_numpy(c.view(np.int32)).cuda() for c in cols]
+               for nm, cols in host_cols.items()}
+    in_tuples = sum(len(r) for r in prog.edb.values())
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def declare(e):
+        for nm, ar in prog.arity.items():
+            e.relation(nm, ar)
+
+    def rules(e):
+        for r in prog.rules:
+            e.rule(r.head, r.body, r.neq)
 
     def step(timing):
         with cdl.Engine(timing=timing) as e:
-            e.relation("edge", 2)
-            e.relation(head, 2)
-            e.load("edge", dev_cols)
-            for r in prog.rules:
-                e.rule(r.head, r.body, r.neq)
+            declare(e)
+            for nm, cols in dev_edb.items():
+                e.load(nm, cols)
+            rules(e)
             st = e.run()
             return st, (e.kernel_profile() if timing else None)
 
@@ -210,7 +247,7 @@ def bench_gb300(args, rank, world, dist):
     clk.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
-    derived, launches, rounds = 0, 0, 0
+    derived, launches, iters = 0, 0, 0
     prof = {}
     for i in range(args.steps):
         if i:
@@ -218,7 +255,7 @@ def bench_gb300(args, rank, world, dist):
         st, pr = step(True)
         derived += st.derived_tuples
         launches += st.kernel_launches
-        rounds = st.iterations
+        iters = st.iterations
         for p in pr:
             q = prof.setdefault(p["kernel"], {"launches": 0, "ms": 0.0, "bytes": 0.0})
             q["launches"] += p["launches"]
@@ -236,22 +273,31 @@ def bench_gb300(args, rank, world, dist):
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         secs, derived = float(mx[0]), int(t[1])
     value = derived / secs
+    per_step = st.derived_tuples
 
     # ---- end to end through the C ABI with host buffers
-    pinned_in = [torch.from_numpy(np.ascontiguousarray(edges[:, k]).view(np.int32)).pin_memory()
-                 for k in range(2)]
-    n_out = st.derived_tuples
-    pinned_out = [torch.empty(max(n_out, 1), dtype=torch.int32, pin_memory=True) for _ in range(2)]
+    pinned_in = {nm: [torch.from_numpy(c.view(np.int32)).pin_memory() for c in cols]
+                 for nm, cols in host_cols.items()}
+    sizes = {}
+    with cdl.Engine() as e:
+        declare(e)
+        for nm, cols in dev_edb.items():
+            e.load(nm, cols)
+        rules(e)
+        e.run()
+        sizes = {nm: e.size(nm) for nm in idb}
+    pinned_out = {nm: [torch.empty(max(sizes[nm], 1), dtype=torch.int32, pin_memory=True)
+                       for _ in range(prog.arity[nm])] for nm in idb}
 
     def step_e2e():
         with cdl.Engine() as e:
-            e.relation("edge", 2)
-            e.relation(head, 2)
-            e.load("edge", pinned_in)
-            for r in prog.rules:
-                e.rule(r.head, r.body, r.neq)
+            declare(e)
+            for nm, cols in pinned_in.items():
+                e.load(nm, cols)
+            rules(e)
             s = e.run()
-            e.export(head, out=[t.data_ptr() for t in pinned_out])
+            for nm in idb:
+                e.export(nm, out=[t.data_ptr() for t in pinned_out[nm]])
             return s
 
     step_e2e()
@@ -267,40 +313,41 @@ def bench_gb300(args, rank, world, dist):
     barrier()
     secs_e2e = e0.elapsed_time(e1) * 1e-3
     e2e = {"value": d_e2e * world / secs_e2e, "unit": "tuples/s",
-           "h2d_bytes_per_step": int(edges.shape[0] * 8), "d2h_bytes_per_step": int(n_out * 8)}
+           "h2d_bytes_per_step": int(sum(4 * c.size for cols in host_cols.values() for c in cols)),
+           "d2h_bytes_per_step": int(sum(4 * sizes[nm] * prog.arity[nm] for nm in idb))}
 
     if rank != 0:
         return
     # ---- roofline of the dominant kernel class
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    name, d = dom
+    name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
     peak, peak_src = measured_peak()
     tr = kernel_traffic(name)
     traffic = None
     if tr is not None:
-        traffic = tr["dram_bytes_per_unit"] * (d["bytes"] / d["launches"]) / tr["algo_bytes_per_unit"]
+        traffic = tr["dram_bytes_per_unit"] / tr["algo_bytes_per_unit"] * d["bytes"] / d["launches"]
     total_ms = sum(v["ms"] for v in prof.values())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": name,
                 "kernel_share": d["ms"] / total_ms, "launches": d["launches"],
                 "peak_source": peak_src}
     # ---- the oracle on a bounded sample, on this host's cores
-    od, osecs = run_oracle_sample(ORACLE_SAMPLE)
+    sspec = spec["sample"]
+    od, osecs = run_oracle_sample(sspec)
     cpu = {"value": od / osecs, "unit": "tuples/s", "cores": 1, "kind": "oracle",
-           "sample": f"same-generation, forest {ORACLE_SAMPLE['n']} nodes (+2% cross edges), "
-                     f"seed {ORACLE_SAMPLE['seed']}: {od} tuples in {osecs:.2f} s, 1 thread "
-                     f"of {os.cpu_count()} host cores"}
+           "sample": describe_sample(sspec, od, osecs) + f", 1 thread of {os.cpu_count()} host cores"}
+    config = {"workload": args.workload, "desc": spec["desc"], "input_tuples": int(in_tuples),
+              "derived_per_step": int(per_step), "iterations": int(iters),
+              "seed": spec["seed"] + rank,
+              "l2": "256 MB buffer written between steps; working set > L2",
+              "parallelism": f"replicas x{world}"}
+    if spec["kind"] == "pt":
+        config["scale"] = args.scale or spec["scale"]
     line = {
         "metric": METRIC, "value": value, "unit": "tuples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic",
-        "config": {"workload": args.workload, "desc": spec["desc"],
-                   "edges": int(edges.shape[0]), "derived_per_step": int(st.derived_tuples),
-                   "iterations": int(rounds), "seed": spec["seed"],
-                   "l2": "256 MB buffer written between steps; working set > L2",
-                   "parallelism": f"replicas x{world}"},
+        "data": "synthetic", "config": config,
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
         "clocks": clocks,
         "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
@@ -317,6 +364,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sg-forest-200k", choices=sorted(WORKLOADS))
+    ap.add_argument("--scale", type=float, default=None, help="points-to scale factor")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -82,10 +82,13 @@ typedef struct {
   uint64_t max_iters;  /* rounds that may produce new tuples; 0 = no limit */
   uint64_t spin_limit; /* iterations of any device-side wait; 0 = default (2^26) */
   uint32_t timing;     /* 1: time every kernel launch with CUDA events */
-  int32_t estimator;   /* join-size estimator: 0 off, 1 on, 2 on + log join stats */
+  int32_t estimator;   /* join-size estimator: 0 off; 1 predict (once trained or set);
+                          2 predict and log every join's features and exact size */
   double hash_load;    /* hash table load factor in (0, 0.9]; 0 = default 0.5 */
-  uint32_t radix_bits; /* radix digit width 4..8; 0 = default 8 */
-  const char* log_path; /* join statistics log (estimator == 2); NULL = none */
+  uint32_t radix_bits; /* radix digit width 8 or 10; 0 = default 8 */
+  const char* log_path; /* reserved, must be NULL */
+  double est_margin;   /* predicted buffers hold 2^(prediction + est_margin) tuples;
+                          0 = default 1.0 (negative values force fallbacks in tests) */
 } cdl_options;
 
 /* Fills *opts with the defaults (everything zero / NULL except the
@@ -172,6 +175,53 @@ cdl_status cdl_kernel_profile(cdl_engine* e, uint32_t idx, char* name, size_t na
 
 /* Engine-owned description of the last error; valid until the next call. */
 const char* cdl_last_error(const cdl_engine* e);
+
+/* ------------------------------------------------------------------------ */
+/* Learned join-size estimator (not in the paper; see the design notes)      */
+/* ------------------------------------------------------------------------ */
+/* A 16 -> 64 -> 64 -> 1 ReLU network predicts log2(1 + join size) from 16
+ * features of each join (sizes, sampled distinct keys, 32-bucket key-hash
+ * histograms of both sides, round, previous sizes, filter flag).  With a
+ * trained network and options.estimator >= 1 the engine sizes each join's
+ * output buffer at 2^(prediction + est_margin) tuples, writes the join in
+ * one pass without Algorithm 1's count and scan, and falls back to the exact
+ * three-pass join when the buffer overflows.  Results never depend on it.
+ * Parameters: CDL_MLP_PARAMS floats, W1 (64x16 row-major), b1 (64), W2
+ * (64x64 row-major), b2 (64), w3 (64), b3 (1). */
+#define CDL_MLP_IN 16
+#define CDL_MLP_PARAMS 5313
+
+/* Copies the logged samples (options.estimator == 2: one per join the
+ * engine ran) into X (n x 16, row-major) and y (log2(1 + exact size)), at
+ * most cap; *n receives the number logged.  X / y may be NULL to query. */
+cdl_status cdl_estimator_log(cdl_engine* e, float* X, float* y, uint64_t cap, uint64_t* n);
+
+/* Trains the network on the GPU from He-uniform weights drawn with seed:
+ * `epochs` full-batch Adam steps (learning rate lr) on the pinball loss at
+ * level tau (e.g. 0.9, so that predictions err on the large side), over the
+ * n host samples X / y, or over the engine's own log when X is NULL.
+ * *loss (may be NULL) receives the final training loss.  The engine then
+ * predicts with the trained network (BF16 copy). */
+cdl_status cdl_estimator_train(cdl_engine* e, const float* X, const float* y, uint64_t n,
+                               uint32_t epochs, float lr, float tau, uint64_t seed, float* loss);
+
+/* Reads (set == 0) or installs (set == 1) the network's FP32 parameters
+ * (host array of CDL_MLP_PARAMS floats). */
+cdl_status cdl_estimator_params(cdl_engine* e, float* params, int set);
+
+/* Network steps on caller-owned device buffers (FP32 parameters, inputs
+ * X n x 16 row-major), for tests and tools; workspace protocol as below. */
+cdl_status cdl_mlp_forward(const float* params, const float* X, uint64_t n, float* out,
+                           void* workspace, size_t* ws_bytes, void* stream);
+/* FP32 forward + backward: out = predictions, grad = d(mean pinball loss at
+ * level tau)/d(params) over the n samples. */
+cdl_status cdl_mlp_gradient(const float* params, const float* X, const float* y, uint64_t n,
+                            float tau, float* out, float* grad, void* workspace, size_t* ws_bytes,
+                            void* stream);
+/* Inference with the parameters rounded to BF16, BF16 activations, FP32
+ * accumulation (the engine's prediction path). */
+cdl_status cdl_mlp_infer_bf16(const float* params, const float* X, uint64_t n, float* out,
+                              void* workspace, size_t* ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Steps of one round on caller-owned device buffers                          */

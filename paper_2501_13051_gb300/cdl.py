@@ -41,7 +41,10 @@ class Options(ctypes.Structure):
                 ("max_iters", ctypes.c_uint64), ("spin_limit", ctypes.c_uint64),
                 ("timing", ctypes.c_uint32), ("estimator", ctypes.c_int32),
                 ("hash_load", ctypes.c_double), ("radix_bits", ctypes.c_uint32),
-                ("log_path", ctypes.c_char_p)]
+                ("log_path", ctypes.c_char_p), ("est_margin", ctypes.c_double)]
+
+MLP_IN = 16
+MLP_PARAMS = 5313
 
 
 class Term(ctypes.Structure):
@@ -116,6 +119,14 @@ def lib():
         "cdl_sort_unique": (ctypes.c_int, [PP, U32, U64, PP, P(U64), VP, P(ctypes.c_size_t), VP]),
         "cdl_diff_merge": (ctypes.c_int, [PP, U64, PP, U64, U32, PP, P(U64), PP, VP,
                                           P(ctypes.c_size_t), VP]),
+        "cdl_estimator_log": (ctypes.c_int, [VP, VP, VP, U64, P(U64)]),
+        "cdl_estimator_train": (ctypes.c_int, [VP, VP, VP, U64, U32, ctypes.c_float,
+                                               ctypes.c_float, U64, P(ctypes.c_float)]),
+        "cdl_estimator_params": (ctypes.c_int, [VP, VP, ctypes.c_int]),
+        "cdl_mlp_forward": (ctypes.c_int, [VP, VP, U64, VP, VP, P(ctypes.c_size_t), VP]),
+        "cdl_mlp_gradient": (ctypes.c_int, [VP, VP, VP, U64, ctypes.c_float, VP, VP, VP,
+                                            P(ctypes.c_size_t), VP]),
+        "cdl_mlp_infer_bf16": (ctypes.c_int, [VP, VP, U64, VP, VP, P(ctypes.c_size_t), VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -177,13 +188,16 @@ class RunStats:
     joins: int
     kernel_launches: int
     delta_per_round: list = field(default_factory=list)
+    est_predictions: int = 0
+    est_overflows: int = 0
 
 
 class Engine:
     """One engine on the current CUDA device and stream (cdl_create)."""
 
     def __init__(self, *, device=None, stream=None, mem_limit=0, max_iters=0, spin_limit=0,
-                 timing=False, hash_load=0.5, radix_bits=8, torch_alloc=True):
+                 timing=False, hash_load=0.5, radix_bits=8, torch_alloc=True, estimator=0,
+                 est_margin=1.0, est_params=None):
         torch = _torch()
         L = lib()
         self._L = L
@@ -202,12 +216,16 @@ class Engine:
         opts.timing = 1 if timing else 0
         opts.hash_load = hash_load
         opts.radix_bits = radix_bits
+        opts.estimator = estimator
+        opts.est_margin = est_margin
         self._opts = opts
         h = ctypes.c_void_p()
         self._check(L.cdl_create(ctypes.byref(opts), ctypes.byref(h)), engine=False)
         self._h = h
         self.rels = {}
         self.arity = {}
+        if est_params is not None:
+            self.estimator_params(est_params)
 
     def _check(self, st, engine=True):
         if st != 0:
@@ -306,7 +324,44 @@ class Engine:
         st.delta_cap = cap
         self._check(self._L.cdl_run(self._h, ctypes.byref(st)))
         return RunStats(st.iterations, st.rounds, st.derived_tuples, st.seconds, st.algo_bytes,
-                        st.joins, st.kernel_launches, [int(buf[i]) for i in range(min(st.rounds, cap))])
+                        st.joins, st.kernel_launches, [int(buf[i]) for i in range(min(st.rounds, cap))],
+                        st.est_predictions, st.est_overflows)
+
+    # ---------------------------------------------------------- estimator
+    def estimator_log(self):
+        """(X, y) of the joins logged so far (options estimator=2)."""
+        n = ctypes.c_uint64()
+        self._check(self._L.cdl_estimator_log(self._h, None, None, 0, ctypes.byref(n)))
+        X = np.zeros((n.value, MLP_IN), dtype=np.float32)
+        y = np.zeros(n.value, dtype=np.float32)
+        self._check(self._L.cdl_estimator_log(self._h, X.ctypes.data, y.ctypes.data, n.value,
+                                              ctypes.byref(n)))
+        return X, y
+
+    def estimator_train(self, X=None, y=None, epochs=2000, lr=3e-3, tau=0.9, seed=1):
+        """Trains the network on the GPU (on X, y, or the engine's own log);
+        returns the final training loss."""
+        loss = ctypes.c_float()
+        if X is None:
+            st = self._L.cdl_estimator_train(self._h, None, None, 0, epochs, lr, tau, seed,
+                                             ctypes.byref(loss))
+        else:
+            X = np.ascontiguousarray(X, dtype=np.float32)
+            y = np.ascontiguousarray(y, dtype=np.float32)
+            st = self._L.cdl_estimator_train(self._h, X.ctypes.data, y.ctypes.data, len(y), epochs,
+                                             lr, tau, seed, ctypes.byref(loss))
+        self._check(st)
+        return float(loss.value)
+
+    def estimator_params(self, params=None):
+        """Reads the trained FP32 parameters, or installs `params`."""
+        if params is None:
+            out = np.zeros(MLP_PARAMS, dtype=np.float32)
+            self._check(self._L.cdl_estimator_params(self._h, out.ctypes.data, 0))
+            return out
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self._L.cdl_estimator_params(self._h, p.ctypes.data, 1))
+        return p
 
     def size(self, name: str) -> int:
         n = ctypes.c_uint64()
@@ -504,3 +559,55 @@ def diff_merge(full_cols, fresh_cols, stream=None):
         raise CdlError(st)
     d = int(nd.value)
     return [x[:d] for x in delta], [x[:nf + d] for x in merged]
+
+
+def _f32(t):
+    torch = _torch()
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float32 tensor")
+    return t
+
+
+def mlp_forward(params, X, stream=None):
+    """FP32 forward of the join-size network: params (5313,), X (n, 16)."""
+    torch = _torch()
+    params, X = _f32(params), _f32(X)
+    n = X.shape[0]
+    out = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+    ws, need = _workspace(lambda w, nb: lib().cdl_mlp_forward(params.data_ptr(), X.data_ptr(), n,
+                                                               out.data_ptr(), w, nb,
+                                                               _stream_handle(stream)))
+    st = lib().cdl_mlp_forward(params.data_ptr(), X.data_ptr(), n, out.data_ptr(), ws.data_ptr(),
+                               ctypes.byref(need), _stream_handle(stream))
+    if st != 0:
+        raise CdlError(st)
+    return out[:n]
+
+
+def mlp_gradient(params, X, y, tau=0.9, stream=None):
+    """FP32 forward + backward: (predictions, d mean pinball loss / d params)."""
+    torch = _torch()
+    params, X, y = _f32(params), _f32(X), _f32(y)
+    n = X.shape[0]
+    out = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    args = (params.data_ptr(), X.data_ptr(), y.data_ptr(), n, tau, out.data_ptr(), grad.data_ptr())
+    ws, need = _workspace(lambda w, nb: lib().cdl_mlp_gradient(*args, w, nb, _stream_handle(stream)))
+    st = lib().cdl_mlp_gradient(*args, ws.data_ptr(), ctypes.byref(need), _stream_handle(stream))
+    if st != 0:
+        raise CdlError(st)
+    return out[:n], grad
+
+
+def mlp_infer_bf16(params, X, stream=None):
+    """The engine's prediction path: BF16 weights / activations, FP32 sums."""
+    torch = _torch()
+    params, X = _f32(params), _f32(X)
+    n = X.shape[0]
+    out = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+    args = (params.data_ptr(), X.data_ptr(), n, out.data_ptr())
+    ws, need = _workspace(lambda w, nb: lib().cdl_mlp_infer_bf16(*args, w, nb, _stream_handle(stream)))
+    st = lib().cdl_mlp_infer_bf16(*args, ws.data_ptr(), ctypes.byref(need), _stream_handle(stream))
+    if st != 0:
+        raise CdlError(st)
+    return out[:n]

@@ -18,11 +18,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -277,6 +279,7 @@ struct Index {
   uint64_t n = 0;
   DBuf table;
   uint64_t slots = 0;
+  uint64_t distinct = 0;  // distinct keys
 };
 
 // A table the join chain reads: columns hold the listed variables.
@@ -298,8 +301,12 @@ struct Src {
 constexpr uint32_t kMaxRels = 1024;
 // control block slots (uint64): 0 error word, 1 scratch, 2 aux cursor,
 // 4 + r fresh cursor of relation r, 4 + kMaxRels + r delta size of r
-constexpr uint32_t kSlotErr = 0, kSlotScratch = 1, kSlotAux = 2, kSlotCursor = 4,
-                   kSlotDelta = 4 + kMaxRels, kCtlSlots = 4 + 2 * kMaxRels;
+// 3 single-pass join size, 4 overflow flag, 8 + r fresh cursor of relation r,
+// 8 + kMaxRels + r delta size of relation r
+constexpr uint32_t kSlotErr = 0, kSlotScratch = 1, kSlotAux = 2, kSlotDirTotal = 3,
+                   kSlotOverflow = 4, kSlotCursor = 8, kSlotDelta = 8 + kMaxRels,
+                   kCtlSlots = 8 + 2 * kMaxRels;
+constexpr int kEstFloats = 32;  // 16 features, the prediction, padding
 
 }  // namespace
 
@@ -320,6 +327,93 @@ struct cdl_engine {
   uint32_t radix_bits = 8;
   double hash_load = 0.5;
   uint64_t joins = 0;
+  // learned join-size estimator
+  DBuf est_w, est_wb, est_io;  // FP32 and BF16 parameters; features + prediction
+  float* h_est = nullptr;      // pinned host mirror of est_io
+  bool est_weights = false;
+  double est_margin = 1.0;
+  uint64_t est_pred = 0, est_over = 0;
+  uint64_t cur_round = 0;
+  std::vector<float> log_x, log_y;
+  std::map<std::tuple<size_t, size_t, size_t>, uint64_t> prev_out;
+  bool est_ready() const { return opt.estimator >= 1 && est_weights; }
+
+  cdl_status install_weights(const float* host) {
+    if (!est_w.p) est_w = alloc(sizeof(float) * kMlpParams);
+    if (!est_wb.p) est_wb = alloc(sizeof(uint16_t) * kMlpParams);
+    if (!est_w.p || !est_wb.p) return fail(CDL_E_NOMEM, "estimator weights");
+    cudaError_t e = cudaSuccess;
+    if (host)
+      e = cudaMemcpyAsync(est_w.p, host, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = mlp_to_bf16(ctx, static_cast<const float*>(est_w.p), est_wb.p);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "estimator weights");
+    est_weights = true;
+    return CDL_OK;
+  }
+
+  // Full-batch Adam on the pinball loss, from He-uniform weights drawn by a
+  // counter-based SplitMix64 stream of the seed.
+  cdl_status train(const float* X, const float* y, uint64_t n, uint32_t epochs, float lr, float tau,
+                   uint64_t seed, float* loss) {
+    if (!X) {
+      X = log_x.data();
+      y = log_y.data();
+      n = log_y.size();
+    }
+    if (n == 0 || !y) return fail(CDL_E_INVALID, "no training samples");
+    std::vector<float> w(kMlpParams, 0.f);
+    auto uni = [&](uint64_t i) {  // uniform in [-1, 1)
+      uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      return (float)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+    };
+    const int H = kMlpHidden, I = kMlpIn;
+    const int oW2 = H * I + H, ow3 = oW2 + H * H + H;
+    for (int i = 0; i < H * I; ++i) w[i] = uni(i) * std::sqrt(6.f / I);
+    for (int i = 0; i < H * H; ++i) w[oW2 + i] = uni(H * I + i) * std::sqrt(6.f / H);
+    for (int i = 0; i < H; ++i) w[ow3 + i] = uni(H * I + H * H + i) * std::sqrt(6.f / H);
+    if (!est_w.p) est_w = alloc(sizeof(float) * kMlpParams);
+    DBuf dX = alloc(sizeof(float) * I * n), dy = alloc(sizeof(float) * n),
+         dout = alloc(sizeof(float) * n), ws = alloc(mlp_workspace(n)),
+         g = alloc(sizeof(float) * kMlpParams), m = alloc(sizeof(float) * kMlpParams),
+         v = alloc(sizeof(float) * kMlpParams);
+    if (!est_w.p || !dX.p || !dy.p || !dout.p || !ws.p || !g.p || !m.p || !v.p)
+      return fail(CDL_E_NOMEM, "estimator training buffers");
+    float* th = static_cast<float*>(est_w.p);
+    cudaError_t e = cudaMemcpyAsync(th, w.data(), sizeof(float) * kMlpParams,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dX.p, X, sizeof(float) * I * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy.p, y, sizeof(float) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.p, 0, sizeof(float) * kMlpParams, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.p, 0, sizeof(float) * kMlpParams, st);
+    for (uint32_t s = 1; s <= epochs && e == cudaSuccess; ++s) {
+      e = mlp_gradient(ctx, th, static_cast<float*>(dX.p), static_cast<float*>(dy.p), n, tau,
+                       static_cast<float*>(dout.p), static_cast<float*>(g.p), ws.p);
+      if (e == cudaSuccess)
+        e = mlp_adam(ctx, th, static_cast<float*>(g.p), static_cast<float*>(m.p),
+                     static_cast<float*>(v.p), s, lr);
+    }
+    std::vector<float> pred(n);
+    if (e == cudaSuccess)
+      e = mlp_forward(ctx, th, static_cast<float*>(dX.p), n, static_cast<float*>(dout.p), ws.p);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(pred.data(), dout.p, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "estimator training");
+    if (loss) {
+      double l = 0;
+      for (uint64_t i = 0; i < n; ++i) {
+        const double r = (double)y[i] - pred[i];
+        l += std::max(tau * r, (tau - 1.0) * r);
+      }
+      *loss = (float)(l / n);
+    }
+    return install_weights(nullptr);
+  }
 
   ~cdl_engine() {
     cache.clear();
@@ -327,6 +421,7 @@ struct cdl_engine {
     ctl.reset();
     pool.release_all();
     if (h_ctl) cudaFreeHost(h_ctl);
+    if (h_est) cudaFreeHost(h_est);
   }
 
   cdl_status fail(cdl_status s, const std::string& m) {
@@ -460,7 +555,8 @@ struct cdl_engine {
     if (e != cudaSuccess) return cuda_fail(e, "count_heads");
     cdl_status r = fetch(kSlotScratch, 1);
     if (r != CDL_OK) return r;
-    ix->slots = table_slots(h_ctl[kSlotScratch], hash_load);
+    ix->distinct = h_ctl[kSlotScratch];
+    ix->slots = table_slots(ix->distinct, hash_load);
     ix->table = alloc(ix->slots * sizeof(Slot));
     if (!ix->table.p) return fail(CDL_E_NOMEM, "hash table");
     e = hash_build(ctx, k0, k1, s.n, static_cast<Slot*>(ix->table.p), ix->slots);
@@ -737,6 +833,7 @@ struct cdl_engine {
       js.probe = P.in();
       js.n_probe = P.n;
       std::unique_ptr<Index> temp_ix;
+      Index* ix = nullptr;
       cdl_status r = CDL_OK;
       if (hkey.empty()) {
         if (B.n > 0xFFFFFFFFull) return fail(CDL_E_CAPACITY, "cross product side too large");
@@ -747,7 +844,6 @@ struct cdl_engine {
         for (uint32_t c = 0; c < B.k; ++c) js.build.c[c] = B.c[c];
         js.slots = 1;
       } else {
-        Index* ix = nullptr;
         r = get_index(B, hkey, &ix, temp_ix);
         if (r != CDL_OK) return r;
         js.pk0 = pkey[0];
@@ -799,6 +895,94 @@ struct cdl_engine {
           next.bits.push_back(from.bits[js.out[k].v]);
         }
       }
+      const bool filter = js.n_neq > 0 || js.n_eq > 0;
+      // features of this join, for the estimator's prediction and its log
+      const std::tuple<size_t, size_t, size_t> step_key{(size_t)(&rule - rules.data()), start, t};
+      const bool feats = ix != nullptr && (est_ready() || opt.estimator >= 2);
+      if (feats) {
+        const Relation* PR = P.rel >= 0 ? rels[P.rel].get() : nullptr;
+        const auto po = prev_out.find(step_key);
+        JoinFeatureHost hf{(float)(PR ? PR->full.n : P.n), (float)ix->distinct, (float)cur_round,
+                           po == prev_out.end() ? 0.f : (float)po->second,
+                           (float)rels[rule.head.rel]->delta.n, filter ? 1.f : 0.f};
+        float* io = static_cast<float*>(est_io.p);
+        cudaError_t e = join_features(ctx, P.c[js.pk0], js.pk1 == 0xFFu ? nullptr : P.c[js.pk1],
+                                      P.n, ix->cols[hkey[0]],
+                                      hkey.size() > 1 ? ix->cols[hkey[1]] : nullptr, B.n, hf, io);
+        if (e == cudaSuccess && est_ready())
+          e = mlp_infer_bf16(ctx, est_wb.p, io, 1, io + kMlpIn);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(h_est, io, sizeof(float) * (kMlpIn + 1), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "join features");
+      }
+      auto log_sample = [&](uint64_t size) {
+        prev_out[step_key] = size;
+        if (!feats || opt.estimator < 2) return;
+        log_x.insert(log_x.end(), h_est, h_est + kMlpIn);
+        log_y.push_back((float)std::log2(1.0 + (double)size));
+      };
+      bool predicted = false;
+      if (feats && est_ready()) {
+        // single pass into a buffer sized by the prediction
+        r = fetch(kSlotScratch, kSlotCursor + (uint32_t)rels.size() - kSlotScratch);
+        if (r != CDL_OK) return r;
+        const double want = std::exp2(std::min(40.0, (double)h_est[kMlpIn] + est_margin));
+        const uint64_t cap = std::max<uint64_t>(256, (uint64_t)std::ceil(want));
+        Relation* H = last ? rels[rule.head.rel].get() : nullptr;
+        const uint64_t cur0 = last ? h_ctl[kSlotCursor + rule.head.rel] : 0;
+        uint64_t* cursor = dslot(last ? kSlotCursor + rule.head.rel : kSlotAux);
+        bool room = true;
+        ColsOut out{};
+        uint64_t out_cap = 0;
+        if (last) {
+          H->fresh_ub = cur0;
+          room = ensure_fresh(*H, cap) == CDL_OK;
+          out = H->fresh.out();
+          out_cap = H->fresh.cap;
+        } else {
+          next.k = js.out_k;
+          room = alloc_cols(next.owned, next.k, cap);
+          out = next.owned.out();
+          out_cap = cap;
+        }
+        if (room) {
+          cudaError_t e = cudaMemsetAsync(dslot(kSlotDirTotal), 0, 16, st);  // total, overflow
+          if (e == cudaSuccess && !last) e = cudaMemsetAsync(cursor, 0, 8, st);
+          if (e == cudaSuccess)
+            e = join_direct(ctx, js, out, cursor, out_cap, dslot(kSlotDirTotal),
+                            reinterpret_cast<uint32_t*>(dslot(kSlotOverflow)));
+          if (e != cudaSuccess) return cuda_fail(e, "single-pass join");
+          r = fetch(kSlotDirTotal, 2);
+          if (r != CDL_OK) return r;
+          const uint64_t total = h_ctl[kSlotDirTotal];
+          if (h_ctl[kSlotOverflow] == 0) {
+            predicted = true;
+            ++est_pred;
+            ++joins;
+            log_sample(total);
+            if (last) return CDL_OK;
+            r = fetch(kSlotAux, 1);
+            if (r != CDL_OK) return r;
+            next.n = next.owned.n = h_ctl[kSlotAux];
+            for (uint32_t k = 0; k < next.k; ++k) next.c[k] = next.owned.c[k];
+            if (next.n == 0) return CDL_OK;
+            left = std::move(next);
+            continue;
+          }
+        }
+        // the prediction was too small: undo the claims, then the exact join
+        ++est_over;
+        if (last) {
+          h_ctl[kSlotScratch] = cur0;
+          cudaError_t e = cudaMemcpyAsync(cursor, h_ctl + kSlotScratch, 8, cudaMemcpyHostToDevice, st);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+          if (e != cudaSuccess) return cuda_fail(e, "cursor rollback");
+          H->fresh_ub = cur0;
+        } else {
+          next.owned.clear();
+        }
+      }
+      (void)predicted;
       // passes 1 and 2: counts, offsets, total
       DBuf off = alloc(std::max<uint64_t>(P.n, 1) * 8);
       DBuf ws = alloc(join_count_workspace(P.n));
@@ -810,8 +994,8 @@ struct cdl_engine {
       if (r != CDL_OK) return r;
       const uint64_t total = h_ctl[kSlotScratch];
       ++joins;
+      log_sample(total);
       if (total == 0) return CDL_OK;
-      const bool filter = js.n_neq > 0 || js.n_eq > 0;
       ws.reset();
       const size_t wws = join_write_workspace(P.n, total);
       DBuf wsp = alloc(wws);
@@ -913,7 +1097,9 @@ struct cdl_engine {
     std::vector<uint64_t> per_round;
     cdl_status status = CDL_OK;
     const uint32_t nr = (uint32_t)rels.size();
+    est_pred = est_over = 0;
     for (uint64_t round = 1; status == CDL_OK; ++round) {
+      cur_round = round;
       cudaError_t e = cudaMemsetAsync(dslot(kSlotCursor), 0, 8 * nr, st);
       if (e != cudaSuccess) {
         status = cuda_fail(e, "round reset");
@@ -996,8 +1182,8 @@ struct cdl_engine {
       stats->algo_bytes = prof.total_bytes;
       stats->joins = joins;
       stats->kernel_launches = prof.total_launches;
-      stats->est_predictions = 0;
-      stats->est_overflows = 0;
+      stats->est_predictions = est_pred;
+      stats->est_overflows = est_over;
       if (stats->delta_per_round)
         for (uint64_t i = 0; i < per_round.size() && i < stats->delta_cap; ++i)
           stats->delta_per_round[i] = per_round[i];
@@ -1071,12 +1257,14 @@ cdl_status cdl_create(const cdl_options* opts, cdl_engine** out) {
   e->hash_load = (e->opt.hash_load > 0 && e->opt.hash_load <= 0.9) ? e->opt.hash_load : 0.5;
   e->radix_bits = e->opt.radix_bits == 10 ? 10 : 8;
   e->prof.on = e->opt.timing != 0;
+  e->est_margin = e->opt.est_margin != 0.0 ? e->opt.est_margin : 1.0;
   if ((e->opt.alloc == nullptr) != (e->opt.free == nullptr)) return CDL_E_INVALID;
   e->ctl = e->alloc(kCtlSlots * sizeof(uint64_t));
-  if (!e->ctl.p) return CDL_E_NOMEM;
-  if (cudaMallocHost(&e->h_ctl, kCtlSlots * sizeof(uint64_t)) != cudaSuccess) {
+  e->est_io = e->alloc(kEstFloats * sizeof(float));
+  if (!e->ctl.p || !e->est_io.p) return CDL_E_NOMEM;
+  if (cudaMallocHost(&e->h_ctl, kCtlSlots * sizeof(uint64_t)) != cudaSuccess ||
+      cudaMallocHost(&e->h_est, kEstFloats * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
-    e->h_ctl = nullptr;
     return CDL_E_CUDA;
   }
   if (cudaMemsetAsync(e->ctl.p, 0, kCtlSlots * sizeof(uint64_t), e->st) != cudaSuccess)
@@ -1205,5 +1393,30 @@ cdl_status cdl_kernel_profile(cdl_engine* e, uint32_t idx, char* name, size_t na
 }
 
 const char* cdl_last_error(const cdl_engine* e) { return e ? e->err.c_str() : "no engine"; }
+
+cdl_status cdl_estimator_log(cdl_engine* e, float* X, float* y, uint64_t cap, uint64_t* n) {
+  if (!e || !n) return CDL_E_INVALID;
+  *n = e->log_y.size();
+  const uint64_t m = std::min<uint64_t>(cap, *n);
+  if (X) std::memcpy(X, e->log_x.data(), sizeof(float) * kMlpIn * m);
+  if (y) std::memcpy(y, e->log_y.data(), sizeof(float) * m);
+  return CDL_OK;
+}
+
+cdl_status cdl_estimator_train(cdl_engine* e, const float* X, const float* y, uint64_t n,
+                               uint32_t epochs, float lr, float tau, uint64_t seed, float* loss) {
+  if (!e || !(tau > 0.f && tau < 1.f) || !(lr > 0.f)) return CDL_E_INVALID;
+  return e->train(X, y, n, epochs, lr, tau, seed, loss);
+}
+
+cdl_status cdl_estimator_params(cdl_engine* e, float* params, int set) {
+  if (!e || !params) return CDL_E_INVALID;
+  if (set) return e->install_weights(params);
+  if (!e->est_weights) return e->fail(CDL_E_STATE, "no trained estimator");
+  cudaError_t er = cudaMemcpyAsync(params, e->est_w.p, sizeof(float) * kMlpParams,
+                                   cudaMemcpyDeviceToHost, e->st);
+  if (er == cudaSuccess) er = cudaStreamSynchronize(e->st);
+  return er == cudaSuccess ? CDL_OK : e->cuda_fail(er, "estimator params");
+}
 
 }  // extern "C"

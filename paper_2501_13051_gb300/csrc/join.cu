@@ -220,6 +220,111 @@ cudaError_t join_count_scan(Ctx& c, const JoinSpec& j, uint64_t* d_off, uint64_t
   return scan_finish(c, counts, j.n_probe, d_off, d_total, scan_ws);
 }
 
+// ------------------------------------------------------------ single pass
+// The write without count and scan, for joins sized by the estimator: a
+// warp takes 32 probe rows, scans their range lengths with shuffles, claims
+// their outputs with one atomic on the cursor and writes them together
+// (lane l writes outputs l, l + 32, ...; the row of an output is found by a
+// five-step search over the warp's offsets), so a hot key is written by 32
+// lanes rather than one.
+constexpr int kDirT = 256;
+
+template <bool FILTER>
+__global__ void __launch_bounds__(kDirT) k_join_direct(const JoinSpec j, ColsOut out,
+                                                       unsigned long long* cursor, uint64_t cap,
+                                                       unsigned long long* total,
+                                                       uint32_t* overflow) {
+  const uint32_t lane = lane_id();
+  const uint32_t lt = lanemask_lt();
+  const uint64_t mask = j.slots - 1;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * kDirT) >> 5;
+  for (uint64_t w = ((uint64_t)blockIdx.x * kDirT + threadIdx.x) >> 5; w * 32 < j.n_probe;
+       w += nwarps) {
+    const uint64_t row = w * 32 + lane;
+    uint32_t st = 0, cnt = 0;
+    if (row < j.n_probe) cnt = lookup(j, mask, row, &st);
+    uint64_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= (uint32_t)o) inc += v;
+    }
+    const uint64_t excl = inc - cnt;
+    const uint64_t wtot = __shfl_sync(0xffffffffu, inc, 31);
+    if (wtot == 0) continue;
+    if (lane == 0) atomicAdd(total, (unsigned long long)wtot);
+    uint64_t base = 0;
+    if (!FILTER) {
+      if (lane == 0) base = atomicAdd(cursor, (unsigned long long)wtot);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base + wtot > cap) {
+        if (lane == 0) atomicOr(overflow, 1u);
+        continue;
+      }
+    }
+    for (uint64_t ob = 0; ob < wtot; ob += 32) {
+      const uint64_t o = ob + lane;
+      const bool valid = o < wtot;
+      // the last lane whose range starts at or before o holds output o
+      uint32_t r = 0;
+#pragma unroll
+      for (uint32_t step = 16; step > 0; step >>= 1) {
+        const uint64_t e = __shfl_sync(0xffffffffu, excl, (r + step) & 31u);
+        if (r + step < 32 && e <= o) r += step;
+      }
+      const uint64_t er = __shfl_sync(0xffffffffu, excl, r);
+      const uint32_t sr = __shfl_sync(0xffffffffu, st, r);
+      const uint64_t prow = w * 32 + r;
+      const uint64_t brow = (uint64_t)sr + (o - er);
+      uint32_t vals[kMaxK] = {0, 0, 0, 0};
+      bool keep = valid;
+      if (valid) {
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k)
+          if (k < (int)j.out_k) vals[k] = ref_value(j, j.out[k], prow, brow);
+        if (FILTER) {
+          for (uint32_t q = 0; q < j.n_eq; ++q)
+            keep &= ref_value(j, j.eq[q][0], prow, brow) == ref_value(j, j.eq[q][1], prow, brow);
+          for (uint32_t q = 0; q < j.n_neq; ++q)
+            keep &= ref_value(j, j.neq[q][0], prow, brow) != ref_value(j, j.neq[q][1], prow, brow);
+        }
+      }
+      uint64_t pos;
+      if (FILTER) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+        uint64_t cb = 0;
+        if (lane == 0 && bal) cb = atomicAdd(cursor, (unsigned long long)__popc(bal));
+        cb = __shfl_sync(0xffffffffu, cb, 0);
+        pos = cb + __popc(bal & lt);
+        if (bal && cb + __popc(bal) > cap && lane == 0) atomicOr(overflow, 1u);
+      } else {
+        pos = base + o;
+      }
+      if (keep && pos < cap) {
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k)
+          if (k < (int)j.out_k) out.c[k][pos] = vals[k];
+      }
+    }
+  }
+}
+
+cudaError_t join_direct(Ctx& c, const JoinSpec& j, ColsOut out, uint64_t* d_cursor,
+                        uint64_t out_cap, uint64_t* d_total, uint32_t* d_overflow) {
+  if (j.n_probe == 0) return cudaSuccess;
+  uint64_t blocks = (j.n_probe + kDirT - 1) / kDirT;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  const bool filter = j.n_neq > 0 || j.n_eq > 0;
+  ProfScope p(c, kJoinDirect, (4.0 + 16.0 + 4.0 * j.out_k) * j.n_probe);
+  auto* cur = reinterpret_cast<unsigned long long*>(d_cursor);
+  auto* tot = reinterpret_cast<unsigned long long*>(d_total);
+  if (filter)
+    k_join_direct<true><<<(unsigned)blocks, kDirT, 0, c.st>>>(j, out, cur, out_cap, tot, d_overflow);
+  else
+    k_join_direct<false><<<(unsigned)blocks, kDirT, 0, c.st>>>(j, out, cur, out_cap, tot, d_overflow);
+  return cudaGetLastError();
+}
+
 size_t join_write_workspace(uint64_t n_probe, uint64_t total) {
   const uint64_t blocks = (n_probe + total + kJTile - 1) / kJTile;
   return ((blocks + 1) * 8 + 255) & ~uint64_t(255);

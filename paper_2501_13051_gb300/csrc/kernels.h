@@ -25,6 +25,8 @@ enum KernelClass : int {
   kDiffMerge,
   kSelect,
   kMisc,
+  kMlp,
+  kJoinDirect,
   kNumClasses
 };
 const char* kernel_class_name(int c);
@@ -179,5 +181,40 @@ cudaError_t select_project(Ctx& c, const SelectSpec& s, ColsOut out, uint64_t* d
 
 // Reserved-value check and column maxima of loaded data.
 cudaError_t check_values(Ctx& c, ColsIn in, uint32_t k, uint64_t n, uint32_t* d_max);
+
+// ------------------------------------------------------------ estimator
+constexpr int kMlpIn = 16, kMlpHidden = 64;
+constexpr int kMlpParams = kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden +
+                           kMlpHidden + 1;
+// Features the host knows about a join (the rest come from key samples).
+struct JoinFeatureHost {
+  float probe_full;      // size of the full version of the probe relation
+  float build_distinct;  // distinct keys of the build side (its index)
+  float round;           // semi-naive round
+  float prev_output;     // exact output of the same rule step in the previous round
+  float prev_delta;      // delta of the head relation in the previous round
+  float filtered;        // 1 when the step filters (inequalities, equalities)
+};
+// workspace of mlp_gradient / mlp_forward for n samples (floats: 4 x 64 n + n)
+inline size_t mlp_workspace(uint64_t n) {
+  return ((4ull * kMlpHidden * (n ? n : 1) + (n ? n : 1)) * sizeof(float) + 255) & ~size_t(255);
+}
+cudaError_t mlp_forward(Ctx& c, const float* th, const float* X, uint64_t n, float* out, void* ws);
+cudaError_t mlp_gradient(Ctx& c, const float* th, const float* X, const float* y, uint64_t n,
+                         float tau, float* out, float* grad, void* ws);
+cudaError_t mlp_adam(Ctx& c, float* th, const float* grad, float* m, float* v, uint64_t step,
+                     float lr);
+cudaError_t mlp_to_bf16(Ctx& c, const float* th, void* tb);
+cudaError_t mlp_infer_bf16(Ctx& c, const void* tb, const float* X, uint64_t n, float* out);
+cudaError_t join_features(Ctx& c, const uint32_t* pk0, const uint32_t* pk1, uint64_t np,
+                          const uint32_t* bk0, const uint32_t* bk1, uint64_t nb,
+                          const JoinFeatureHost& hf, float* f);
+
+// Single-pass join write sized by a prediction: every probe row claims its
+// range at *d_cursor (atomic, one per warp); survivors are written when the
+// claim fits below out_cap, else *d_overflow is set and nothing more of that
+// warp is written.  *d_total receives the unfiltered join size.
+cudaError_t join_direct(Ctx& c, const JoinSpec& j, ColsOut out, uint64_t* d_cursor,
+                        uint64_t out_cap, uint64_t* d_total, uint32_t* d_overflow);
 
 }  // namespace cdl

@@ -242,6 +242,52 @@ cdl_status cdl_sort_unique(const uint32_t* const* cols, uint32_t arity, uint64_t
   return CDL_OK;
 }
 
+cdl_status cdl_mlp_forward(const float* params, const float* X, uint64_t n, float* out,
+                           void* workspace, size_t* ws_bytes, void* stream) {
+  if (!ws_bytes) return CDL_E_INVALID;
+  const size_t need = mlp_workspace(n);
+  if (!workspace) {
+    *ws_bytes = need;
+    return CDL_OK;
+  }
+  if (*ws_bytes < need || !params || ((!X || !out) && n)) return CDL_E_INVALID;
+  Ctx c;
+  c.st = static_cast<cudaStream_t>(stream);
+  return cuda_status(mlp_forward(c, params, X, n, out, workspace));
+}
+
+cdl_status cdl_mlp_gradient(const float* params, const float* X, const float* y, uint64_t n,
+                            float tau, float* out, float* grad, void* workspace, size_t* ws_bytes,
+                            void* stream) {
+  if (!ws_bytes) return CDL_E_INVALID;
+  const size_t need = mlp_workspace(n);
+  if (!workspace) {
+    *ws_bytes = need;
+    return CDL_OK;
+  }
+  if (*ws_bytes < need || !params || !grad || ((!X || !y || !out) && n)) return CDL_E_INVALID;
+  if (!(tau > 0.f && tau < 1.f)) return CDL_E_INVALID;
+  Ctx c;
+  c.st = static_cast<cudaStream_t>(stream);
+  return cuda_status(mlp_gradient(c, params, X, y, n, tau, out, grad, workspace));
+}
+
+cdl_status cdl_mlp_infer_bf16(const float* params, const float* X, uint64_t n, float* out,
+                              void* workspace, size_t* ws_bytes, void* stream) {
+  if (!ws_bytes) return CDL_E_INVALID;
+  const size_t need = up(sizeof(uint16_t) * kMlpParams);
+  if (!workspace) {
+    *ws_bytes = need;
+    return CDL_OK;
+  }
+  if (*ws_bytes < need || !params || ((!X || !out) && n)) return CDL_E_INVALID;
+  Ctx c;
+  c.st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = mlp_to_bf16(c, params, workspace);
+  if (e == cudaSuccess) e = mlp_infer_bf16(c, workspace, X, n, out);
+  return cuda_status(e);
+}
+
 cdl_status cdl_diff_merge(const uint32_t* const* full, uint64_t n_full,
                           const uint32_t* const* fresh, uint64_t n_fresh, uint32_t arity,
                           uint32_t* const* delta, uint64_t* n_delta, uint32_t* const* merged,

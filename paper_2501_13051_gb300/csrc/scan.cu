@@ -81,6 +81,37 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
   }
 }
 
+// Small inputs: one block walks the whole array with a running carry, so
+// the scan is one launch instead of three.
+constexpr uint64_t kSmallScan = 1 << 16;
+
+__global__ void __launch_bounds__(kTopThreads) k_scan_small(const uint32_t* __restrict__ in,
+                                                            uint64_t n, uint64_t* __restrict__ out,
+                                                            uint64_t* __restrict__ d_total) {
+  __shared__ uint64_t red[kTopThreads / 32 + 1];
+  constexpr int kI = 4;
+  uint64_t carry = 0;
+  for (uint64_t b = 0; b < n; b += (uint64_t)kTopThreads * kI) {
+    const uint64_t first = b + (uint64_t)threadIdx.x * kI;
+    uint32_t v[kI];
+    uint64_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kI; ++q) {
+      v[q] = first + q < n ? __ldg(in + first + q) : 0u;
+      s += v[q];
+    }
+    uint64_t tot;
+    uint64_t run = carry + block_exclusive_sum<kTopThreads, uint64_t>(s, red, &tot);
+#pragma unroll
+    for (int q = 0; q < kI; ++q) {
+      if (first + q < n) out[first + q] = run;
+      run += v[q];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && d_total) *d_total = carry;
+}
+
 }  // namespace
 
 size_t scan_workspace(uint64_t n) {
@@ -94,6 +125,7 @@ cudaError_t exclusive_scan(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out
     if (d_total) return cudaMemsetAsync(d_total, 0, sizeof(uint64_t), c.st);
     return cudaSuccess;
   }
+  if (n <= kSmallScan) return scan_finish(c, in, n, out, d_total, ws);
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
   uint64_t* sums = static_cast<uint64_t*>(ws);
   {
@@ -109,9 +141,13 @@ cudaError_t scan_finish(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out, u
     if (d_total) return cudaMemsetAsync(d_total, 0, sizeof(uint64_t), c.st);
     return cudaSuccess;
   }
+  ProfScope p(c, kScan, 4.0 * n + 8.0 * n);
+  if (n <= kSmallScan) {  // tile sums, if any were stored, are not needed
+    k_scan_small<<<1, kTopThreads, 0, c.st>>>(in, n, out, d_total);
+    return cudaGetLastError();
+  }
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
   uint64_t* sums = static_cast<uint64_t*>(ws);
-  ProfScope p(c, kScan, 4.0 * n + 8.0 * n);
   k_scan_top<<<1, kTopThreads, 0, c.st>>>(sums, tiles, d_total);
   k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, c.st>>>(in, n, sums, out);
   return cudaGetLastError();

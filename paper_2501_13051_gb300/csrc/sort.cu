@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kRT) k_radix_scatter(ColsIn in, ColsOut out, u
       s += t;
     }
     tstart[d] = s;
-    gstart[d] = off[(uint64_t)d * ntiles + blockIdx.x];
+    gstart[d] = off ? off[(uint64_t)d * ntiles + blockIdx.x] : 0ull;
   }
   __syncthreads();
   {  // tile-local digit starts: exclusive scan of the digit totals
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kRT) k_radix_scatter(ColsIn in, ColsOut out, u
 #pragma unroll
     for (int k = 0; k < K; ++k) t[k] = stage[k * kRTile + i];
     const uint32_t d = digit_of<K>(t, p);
-    const uint64_t g = gstart[d] + (i - tstart[d]);
+    const uint64_t g = off ? gstart[d] + (i - tstart[d]) : (uint64_t)i;
 #pragma unroll
     for (int k = 0; k < K; ++k) out.c[k][g] = t[k];
   }
@@ -194,15 +194,20 @@ cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uin
     for (int k = 0; k < kMaxK; ++k) in.c[k] = src.c[k];
     uint32_t cols_used = 0;
     for (int k = 0; k < K; ++k) cols_used += p.mask[k] != 0;
-    {
-      ProfScope ps(c, kRadixUpsweep, 4.0 * cols_used * n + 4.0 * cells);
-      k_radix_upsweep<K, BITS><<<(unsigned)ntiles, kRT, 0, c.st>>>(in, n, p, hist, ntiles);
+    // one tile: its own ranking is the global order, no histogram pass
+    const bool single = ntiles == 1;
+    if (!single) {
+      {
+        ProfScope ps(c, kRadixUpsweep, 4.0 * cols_used * n + 4.0 * cells);
+        k_radix_upsweep<K, BITS><<<(unsigned)ntiles, kRT, 0, c.st>>>(in, n, p, hist, ntiles);
+      }
+      e = exclusive_scan(c, hist, cells, off, nullptr, scan_ws);
+      if (e != cudaSuccess) return e;
     }
-    e = exclusive_scan(c, hist, cells, off, nullptr, scan_ws);
-    if (e != cudaSuccess) return e;
     {
       ProfScope ps(c, kRadixScatter, 8.0 * K * n);
-      k_radix_scatter<K, BITS><<<(unsigned)ntiles, kRT, smem, c.st>>>(in, dst, n, p, off, ntiles);
+      k_radix_scatter<K, BITS><<<(unsigned)ntiles, kRT, smem, c.st>>>(in, dst, n, p,
+                                                                     single ? nullptr : off, ntiles);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -1,0 +1,152 @@
+"""The learned join-size estimator on the GPU: gradients and BF16 inference
+against the float64 oracle (oracle.mlp), and the engine's predicted
+single-pass joins: trained on logged joins, bit-exact fixpoints, fewer
+launches than the exact count-scan-write joins, a lower prediction loss
+than the estimators it learns from, and exact fallback on forced
+under-prediction."""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from paper_2501_13051_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cdl():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a GPU"
+    from paper_2501_13051_gb300 import build as B
+    B.build()
+    from paper_2501_13051_gb300 import cdl as C
+    return C
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def batch(seed, n):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0, 20, size=(n, M.D_IN)).astype(np.float32)
+    y = rng.uniform(0, 25, size=n).astype(np.float32)
+    theta = (M.init(seed) * 0.5).astype(np.float32)
+    return theta, X, y
+
+
+@pytest.mark.parametrize("n,tau", [(1, 0.9), (37, 0.9), (500, 0.5), (2000, 0.1)])
+def test_gradient_matches_oracle(cdl, n, tau):
+    theta, X, y = batch(n, n)
+    out, grad = cdl.mlp_gradient(dev(theta), dev(X), dev(y), tau)
+    pred, _ = M.forward(theta.astype(np.float64), X.astype(np.float64))
+    _, g = M.gradient(theta.astype(np.float64), X.astype(np.float64), y.astype(np.float64), tau)
+    out, grad = out.cpu().numpy(), grad.cpu().numpy()
+    assert np.all(np.abs(out - pred) <= 1e-4 * (1 + np.abs(pred)))
+    # FP32 sums over <= 2000 samples of <= 64 terms: relative error well under 1e-4
+    assert np.linalg.norm(grad - g) <= 1e-4 * np.linalg.norm(g)
+    assert np.all(np.abs(grad - g) <= 1e-4 * np.abs(g).max() + 1e-7)
+    fwd = cdl.mlp_forward(dev(theta), dev(X)).cpu().numpy()
+    assert np.array_equal(fwd, out)
+
+
+def test_bf16_inference(cdl):
+    theta, X, y = batch(5, 300)
+    got = cdl.mlp_infer_bf16(dev(theta), dev(X)).cpu().numpy()
+    ref = M.forward_bf16(theta, X)
+    # same roundings; only the FP32 summation order differs, which may move a
+    # hidden value across a BF16 rounding boundary (one BF16 ulp, 2^-8)
+    assert np.all(np.abs(got - ref) <= 2e-3 * (1 + np.abs(ref)))
+    fp, _ = M.forward(theta.astype(np.float64), X.astype(np.float64))
+    assert np.median(np.abs(got - fp) / (1 + np.abs(fp))) <= 0.01
+
+
+def log_joins(cdl, programs):
+    X, y = [], []
+    for prog in programs:
+        with cdl.Engine(estimator=2) as e:
+            e.load_program(prog)
+            e.run()
+            a, b = e.estimator_log()
+            X.append(a)
+            y.append(b)
+    return np.concatenate(X), np.concatenate(y)
+
+
+def training_programs():
+    progs = [W.tc_program(W.er_graph(n, m, s)) for n, m, s in
+             ((300, 450, 1), (600, 900, 2), (1000, 1500, 3), (800, 1000, 4), (1500, 2000, 5))]
+    progs += [W.sg_program(W.random_forest(n, s)) for n, s in ((2000, 6), (4000, 7), (8000, 8))]
+    progs += [W.points_to_program(W.points_to_edb(1 / 4096, 9))]
+    return progs
+
+
+@pytest.fixture(scope="module")
+def trained(cdl):
+    X, y = log_joins(cdl, training_programs())
+    assert len(y) > 100
+    with cdl.Engine() as e:
+        loss = e.estimator_train(X, y, epochs=3000, lr=3e-3, tau=0.9, seed=1)
+        params = e.estimator_params()
+    return X, y, params, loss
+
+
+def test_trained_network_beats_its_inputs(cdl, trained):
+    """What the network gains: its pinball loss (tau 0.9) on the logged joins
+    against (a) the histogram join estimate it gets as feature 6, (b) the
+    previous round's size of the same join step (feature 13) and (c) the best
+    constant."""
+    X, y, params, loss = trained
+    tau = 0.9
+    pred = cdl.mlp_infer_bf16(dev(params), dev(X)).cpu().numpy()
+    l_net = M.pinball(pred, y, tau)
+    l_hist = M.pinball(X[:, 6], y, tau)
+    l_prev = M.pinball(X[:, 13], y, tau)
+    l_const = M.pinball(np.full_like(y, np.quantile(y, tau)), y, tau)
+    assert l_net < 0.8 * min(l_hist, l_prev, l_const), (l_net, l_hist, l_prev, l_const)
+    assert loss == pytest.approx(M.pinball(M.forward(params.astype(np.float64), X)[0], y, tau),
+                                 rel=1e-3, abs=1e-3)
+
+
+@pytest.mark.parametrize("make", [lambda: W.sg_program(W.random_forest(6000, 99)),
+                                  lambda: W.tc_program(W.er_graph(1200, 1700, 98)),
+                                  lambda: W.points_to_program(W.points_to_edb(1 / 4096, 97))])
+def test_predicted_joins_are_exact_and_cheaper(cdl, oracle_lib, trained, make):
+    _, _, params, _ = trained
+    prog = make()
+    want = oracle_lib.run_program(prog)
+    exact, st0 = cdl.run_program(prog)
+    with cdl.Engine(estimator=1, est_params=params) as e:
+        e.load_program(prog)
+        st = e.run()
+        got = {nm: e.export(nm) for nm in prog.arity}
+    for nm in prog.arity:
+        assert np.array_equal(got[nm], want.relations[nm]), nm
+    assert st.iterations == want.iterations and st.delta_per_round == st0.delta_per_round
+    assert st.est_predictions > 0
+    assert st.est_overflows <= st.est_predictions  # fallbacks are the exception
+    # no count pass, no scan, no offsets: the joins move fewer bytes
+    assert st.algo_bytes < st0.algo_bytes
+
+
+def test_forced_underprediction_falls_back_exactly(cdl, oracle_lib, trained):
+    _, _, params, _ = trained
+    prog = W.sg_program(W.random_forest(5000, 11))
+    want = oracle_lib.run_program(prog)
+    with cdl.Engine(estimator=1, est_params=params, est_margin=-40.0) as e:
+        e.load_program(prog)
+        st = e.run()
+        got = e.export("sg")
+    assert np.array_equal(got, want.relations["sg"])
+    assert st.est_overflows > 0 and st.iterations == want.iterations
+
+
+def test_estimator_without_weights_is_exact(cdl, oracle_lib):
+    prog = W.tc_program(W.er_graph(200, 300, 3))
+    with cdl.Engine(estimator=1) as e:
+        e.load_program(prog)
+        st = e.run()
+        got = e.export("path")
+    assert st.est_predictions == 0
+    assert np.array_equal(got, oracle_lib.run_program(prog).relations["path"])
