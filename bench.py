@@ -63,6 +63,11 @@ WORKLOADS = {
                        desc="OWL-2-RL-style rules over 20M synthetic triples, 5M entities, "
                             "500 classes, 200 properties, 193 rule instances",
                        sample=dict(kind="owl", triples=1_000_000, seed=4)),
+    "batched-512": dict(kind="batch", count=512, seed=5, lo=1e3, hi=5e5,
+                        desc="512 independent fixpoints in one batched run (instance column "
+                             "leading): TC on even, SG on odd instances, directed ER graphs "
+                             "with log-uniform 1e3..5e5 edges, mean out-degree 0.9",
+                        sample=dict(kind="batch", count=16, seed=5, lo=1e3, hi=2e4)),
 }
 METRIC = "derived tuples/s per fixpoint"
 
@@ -80,14 +85,46 @@ def make_program(spec, seed_offset=0, scale=None):
         t = spec["triples"]
         f = t / 20_000_000
         return W.owl_program(*W.owl_triples(t, seed, n_entities=max(1000, int(5_000_000 * f))))
+    if kind == "batch":
+        return W.batched_program(*W.batched_instances(spec["count"], seed, spec["lo"], spec["hi"]))
     raise ValueError(kind)
+
+
+def sequential_baseline(spec, seed_offset=0):
+    """The batched workload's instances run one after another, each as its
+    own engine (the plain exact form): derived tuples and device seconds."""
+    import torch
+
+    from paper_2501_13051_gb300 import cdl
+    graphs, kinds = W.batched_instances(spec["count"], spec["seed"] + seed_offset, spec["lo"],
+                                        spec["hi"])
+    progs = [W.tc_program(g) if k == "tc" else W.sg_program(g) for g, k in zip(graphs, kinds)]
+    dev = [[torch.from_numpy(np.ascontiguousarray(p.edb["edge"][:, k]).view(np.int32)).cuda()
+            for k in range(2)] for p in progs]
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    derived = 0
+    for p, d in zip(progs, dev):
+        with cdl.Engine() as e:
+            for nm, ar in p.arity.items():
+                e.relation(nm, ar)
+            e.load("edge", d)
+            for r in p.rules:
+                e.rule(r.head, r.body, r.neq)
+            derived += e.run().derived_tuples
+    b.record()
+    torch.cuda.synchronize()
+    return derived, a.elapsed_time(b) * 1e-3
 
 
 def describe_sample(spec, derived, secs):
     what = {"sg": lambda s: f"same-generation, forest {s['n']} nodes (+2% cross edges)",
             "tc": lambda s: f"transitive closure, ER {s['n']} nodes / {s['m']} edges",
             "pt": lambda s: f"points-to at scale {s['scale']:g}",
-            "owl": lambda s: f"OWL-RL rules over {s['triples']} triples"}[spec["kind"]](spec)
+            "owl": lambda s: f"OWL-RL rules over {s['triples']} triples",
+            "batch": lambda s: f"{s['count']} batched TC/SG instances, {s['lo']:g}..{s['hi']:g} "
+                               f"edges"}[spec["kind"]](spec)
     return f"{what}, seed {spec['seed']}: {derived} tuples in {secs:.2f} s"
 
 
@@ -215,6 +252,7 @@ def bench_gb300(args, rank, world, dist):
     dev_edb = {nm: [torch.from_numpy(c.view(np.int32)).cuda() for c in cols]
                for nm, cols in host_cols.items()}
     in_tuples = sum(len(r) for r in prog.edb.values())
+    ninst = spec["count"] if spec["kind"] == "batch" else 0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def declare(e):
@@ -226,7 +264,7 @@ def bench_gb300(args, rank, world, dist):
             e.rule(r.head, r.body, r.neq)
 
     def step(timing):
-        with cdl.Engine(timing=timing) as e:
+        with cdl.Engine(timing=timing, n_instances=ninst) as e:
             declare(e)
             for nm, cols in dev_edb.items():
                 e.load(nm, cols)
@@ -279,7 +317,7 @@ def bench_gb300(args, rank, world, dist):
     pinned_in = {nm: [torch.from_numpy(c.view(np.int32)).pin_memory() for c in cols]
                  for nm, cols in host_cols.items()}
     sizes = {}
-    with cdl.Engine() as e:
+    with cdl.Engine(n_instances=ninst) as e:
         declare(e)
         for nm, cols in dev_edb.items():
             e.load(nm, cols)
@@ -290,7 +328,7 @@ def bench_gb300(args, rank, world, dist):
                        for _ in range(prog.arity[nm])] for nm in idb}
 
     def step_e2e():
-        with cdl.Engine() as e:
+        with cdl.Engine(n_instances=ninst) as e:
             declare(e)
             for nm, cols in pinned_in.items():
                 e.load(nm, cols)
@@ -343,6 +381,13 @@ def bench_gb300(args, rank, world, dist):
               "parallelism": f"replicas x{world}"}
     if spec["kind"] == "pt":
         config["scale"] = args.scale or spec["scale"]
+    if spec["kind"] == "batch":
+        sd, ss = sequential_baseline(spec, seed_offset=rank)
+        config["instances"] = spec["count"]
+        config["max_iterations_per_instance"] = int(max(st.iters_per_instance))
+        config["sequential_plain"] = {"tuples_per_s": sd / ss, "seconds": ss,
+                                      "derived": int(sd)}
+        config["batched_over_sequential"] = value / (sd / ss)
     line = {
         "metric": METRIC, "value": value, "unit": "tuples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,

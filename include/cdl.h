@@ -89,6 +89,8 @@ typedef struct {
   const char* log_path; /* reserved, must be NULL */
   double est_margin;   /* predicted buffers hold 2^(prediction + est_margin) tuples;
                           0 = default 1.0 (negative values force fallbacks in tests) */
+  uint32_t n_instances; /* > 0: batched independent fixpoints; column 0 of every derived
+                           relation is an instance id < n_instances (see cdl_stats) */
 } cdl_options;
 
 /* Fills *opts with the defaults (everything zero / NULL except the
@@ -151,6 +153,8 @@ typedef struct {
   uint64_t est_overflows;   /* of those, joins that fell back to the exact count */
   uint64_t* delta_per_round; /* caller array or NULL: new tuples per round */
   uint64_t delta_cap;        /* its length */
+  uint64_t* iters_per_instance; /* caller array of n_instances or NULL: for a batched run,
+                                   the last round in which each instance derived a tuple */
 } cdl_stats;
 
 /* Runs the semi-naive loop to the fixpoint on the engine's stream and waits

@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
                 ("max_iters", ctypes.c_uint64), ("spin_limit", ctypes.c_uint64),
                 ("timing", ctypes.c_uint32), ("estimator", ctypes.c_int32),
                 ("hash_load", ctypes.c_double), ("radix_bits", ctypes.c_uint32),
-                ("log_path", ctypes.c_char_p), ("est_margin", ctypes.c_double)]
+                ("log_path", ctypes.c_char_p), ("est_margin", ctypes.c_double),
+                ("n_instances", ctypes.c_uint32)]
 
 MLP_IN = 16
 MLP_PARAMS = 5313
@@ -68,7 +69,8 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64), ("est_predictions", ctypes.c_uint64),
                 ("est_overflows", ctypes.c_uint64),
                 ("delta_per_round", ctypes.POINTER(ctypes.c_uint64)),
-                ("delta_cap", ctypes.c_uint64)]
+                ("delta_cap", ctypes.c_uint64),
+                ("iters_per_instance", ctypes.POINTER(ctypes.c_uint64))]
 
 
 class ColRef(ctypes.Structure):
@@ -190,6 +192,7 @@ class RunStats:
     delta_per_round: list = field(default_factory=list)
     est_predictions: int = 0
     est_overflows: int = 0
+    iters_per_instance: list = field(default_factory=list)
 
 
 class Engine:
@@ -197,7 +200,7 @@ class Engine:
 
     def __init__(self, *, device=None, stream=None, mem_limit=0, max_iters=0, spin_limit=0,
                  timing=False, hash_load=0.5, radix_bits=8, torch_alloc=True, estimator=0,
-                 est_margin=1.0, est_params=None):
+                 est_margin=1.0, est_params=None, n_instances=0):
         torch = _torch()
         L = lib()
         self._L = L
@@ -218,6 +221,8 @@ class Engine:
         opts.radix_bits = radix_bits
         opts.estimator = estimator
         opts.est_margin = est_margin
+        opts.n_instances = n_instances
+        self.n_instances = n_instances
         self._opts = opts
         h = ctypes.c_void_p()
         self._check(L.cdl_create(ctypes.byref(opts), ctypes.byref(h)), engine=False)
@@ -322,10 +327,14 @@ class Engine:
         st = Stats()
         st.delta_per_round = ctypes.cast(buf, ctypes.POINTER(ctypes.c_uint64))
         st.delta_cap = cap
+        inst = (ctypes.c_uint64 * max(1, self.n_instances))()
+        if self.n_instances:
+            st.iters_per_instance = ctypes.cast(inst, ctypes.POINTER(ctypes.c_uint64))
         self._check(self._L.cdl_run(self._h, ctypes.byref(st)))
         return RunStats(st.iterations, st.rounds, st.derived_tuples, st.seconds, st.algo_bytes,
                         st.joins, st.kernel_launches, [int(buf[i]) for i in range(min(st.rounds, cap))],
-                        st.est_predictions, st.est_overflows)
+                        st.est_predictions, st.est_overflows,
+                        [int(inst[i]) for i in range(self.n_instances)])
 
     # ---------------------------------------------------------- estimator
     def estimator_log(self):

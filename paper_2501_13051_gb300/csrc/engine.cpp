@@ -336,6 +336,7 @@ struct cdl_engine {
   uint64_t cur_round = 0;
   std::vector<float> log_x, log_y;
   std::map<std::tuple<size_t, size_t, size_t>, uint64_t> prev_out;
+  DBuf inst_last;  // batched runs: last round each instance derived a tuple
   bool est_ready() const { return opt.estimator >= 1 && est_weights; }
 
   cdl_status install_weights(const float* host) {
@@ -1098,6 +1099,12 @@ struct cdl_engine {
     cdl_status status = CDL_OK;
     const uint32_t nr = (uint32_t)rels.size();
     est_pred = est_over = 0;
+    if (opt.n_instances) {
+      inst_last = alloc(sizeof(uint64_t) * opt.n_instances);
+      if (!inst_last.p) return fail(CDL_E_NOMEM, "instance marks");
+      if (cudaMemsetAsync(inst_last.p, 0, sizeof(uint64_t) * opt.n_instances, st) != cudaSuccess)
+        return fail(CDL_E_CUDA, "instance marks");
+    }
     for (uint64_t round = 1; status == CDL_OK; ++round) {
       cur_round = round;
       cudaError_t e = cudaMemsetAsync(dslot(kSlotCursor), 0, 8 * nr, st);
@@ -1149,7 +1156,16 @@ struct cdl_engine {
         R.full.n += nd;
         if (R.fresh.n) prof.add_bytes(kDiffMerge, 8.0 * R.arity * nd);
         new_total += nd;
+        if (opt.n_instances && nd) {  // batched: instances that derived in this round
+          cudaError_t e = mark_instances(ctx, R.delta.c[0], nd, opt.n_instances,
+                                         static_cast<uint64_t*>(inst_last.p), round);
+          if (e != cudaSuccess) {
+            status = cuda_fail(e, "instance marks");
+            break;
+          }
+        }
       }
+      if (status != CDL_OK) break;
       evict_stale();
       rounds = round;
       per_round.push_back(new_total);
@@ -1187,6 +1203,12 @@ struct cdl_engine {
       if (stats->delta_per_round)
         for (uint64_t i = 0; i < per_round.size() && i < stats->delta_cap; ++i)
           stats->delta_per_round[i] = per_round[i];
+      if (stats->iters_per_instance && opt.n_instances && inst_last.p && status == CDL_OK) {
+        cudaError_t e = cudaMemcpyAsync(stats->iters_per_instance, inst_last.p,
+                                        sizeof(uint64_t) * opt.n_instances, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) status = cuda_fail(e, "instance iterations");
+      }
     }
     return status;
   }

@@ -179,6 +179,11 @@ struct SelectSpec {
 cudaError_t select_project(Ctx& c, const SelectSpec& s, ColsOut out, uint64_t* d_cursor,
                            uint64_t out_cap);
 
+// last_round[v] = round for every instance id v < n_instances present in the
+// sorted instance column inst (n rows).
+cudaError_t mark_instances(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,
+                           uint64_t* last_round, uint64_t round);
+
 // Reserved-value check and column maxima of loaded data.
 cudaError_t check_values(Ctx& c, ColsIn in, uint32_t k, uint64_t n, uint32_t* d_max);
 

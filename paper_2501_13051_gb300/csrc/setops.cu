@@ -73,7 +73,28 @@ __global__ void k_check_values(ColsIn in, uint32_t k, uint64_t n, uint32_t* d_ma
   }
 }
 
+// Batched fixpoints: the delta of a relation whose column 0 is an instance
+// id is sorted by instance, so every run head marks an instance that derived
+// something in this round.
+__global__ void k_mark_instances(const uint32_t* __restrict__ inst, uint64_t n,
+                                 uint32_t n_instances, uint64_t* __restrict__ last_round,
+                                 uint64_t round) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t v = __ldg(inst + i);
+  if ((i == 0 || __ldg(inst + i - 1) != v) && v < n_instances) last_round[v] = round;
+}
+
 }  // namespace
+
+cudaError_t mark_instances(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,
+                           uint64_t* last_round, uint64_t round) {
+  if (n == 0) return cudaSuccess;
+  ProfScope p(c, kMisc, 4.0 * n);
+  k_mark_instances<<<(unsigned)((n + 255) / 256), 256, 0, c.st>>>(inst, n, n_instances, last_round,
+                                                                  round);
+  return cudaGetLastError();
+}
 
 cudaError_t select_project(Ctx& c, const SelectSpec& s, ColsOut out, uint64_t* d_cursor,
                            uint64_t out_cap) {

@@ -263,6 +263,23 @@ def batched_graph_sizes(count: int, seed: int, lo: float = 1e3, hi: float = 5e5)
     return np.floor(np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))).astype(np.int64)
 
 
+def batched_instances(count: int, seed: int, lo: float = 1e3, hi: float = 5e5,
+                      degree: float = 0.9):
+    """``count`` independent instances for batched fixpoints: instance i is
+    transitive closure (even i) or same generation (odd i) on a directed
+    Erdos-Renyi graph with E_i edges, E_i log-uniform in [lo, hi], over
+    ceil(E_i / degree) nodes (mean out-degree ``degree``), graph seed
+    1000 * seed + i.  Returns (graphs, kinds)."""
+    sizes = batched_graph_sizes(count, seed, lo, hi)
+    graphs, kinds = [], []
+    for i, e in enumerate(sizes):
+        e = int(e)
+        n = int(math.ceil(e / degree))
+        graphs.append(er_graph(n, e, 1000 * seed + i))
+        kinds.append("tc" if i % 2 == 0 else "sg")
+    return graphs, kinds
+
+
 # --------------------------------------------------------------------------
 # programs
 # --------------------------------------------------------------------------
