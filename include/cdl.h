@@ -81,7 +81,10 @@ typedef struct {
   uint64_t mem_limit;  /* bytes of device memory the engine may hold; 0 = no limit */
   uint64_t max_iters;  /* rounds that may produce new tuples; 0 = no limit */
   uint64_t spin_limit; /* iterations of any device-side wait; 0 = default (2^26) */
-  uint32_t timing;     /* 1: time every kernel launch with CUDA events */
+  uint32_t timing;     /* CUDA-event timing of kernel launches: 0 off; 1 every kernel
+                          class; any other value is a mask, bit (1 + c) timing class c
+                          (the classes cdl_kernel_profile lists), so that events wrap
+                          only the launches one wants timed */
   int32_t estimator;   /* join-size estimator: 0 off; 1 predict (once trained or set);
                           2 predict and log every join's features and exact size */
   double hash_load;    /* hash table load factor in (0, 0.9]; 0 = default 0.5 */
@@ -89,8 +92,20 @@ typedef struct {
   const char* log_path; /* reserved, must be NULL */
   double est_margin;   /* predicted buffers hold 2^(prediction + est_margin) tuples;
                           0 = default 1.0 (negative values force fallbacks in tests) */
-  uint32_t n_instances; /* > 0: batched independent fixpoints; column 0 of every derived
-                           relation is an instance id < n_instances (see cdl_stats) */
+  uint32_t n_instances; /* > 0: batched independent fixpoints.  Column 0 of every
+                           relation holds an instance id < n_instances (CDL_E_VALUE at
+                           cdl_run otherwise) and every rule has one variable in column 0
+                           of its head and of each body atom (CDL_E_INVALID otherwise);
+                           per-instance iteration counts in cdl_stats */
+  int32_t retire;       /* batched runs: 0 = default, the rows of an instance that reached
+                           its fixpoint leave the merged relation until the end of the
+                           run; -1 = every instance stays in it every round */
+  int32_t autotune;     /* launch-parameter tuner (radix digit width and block size, hash
+                           load factor): 0 off (the values above); 1 use what tune_cache
+                           holds; 2 also time untried candidates (CUDA events) and write
+                           the results back to tune_cache at the end of cdl_run.  Results
+                           never depend on it */
+  const char* tune_cache; /* tuner file path (copied at cdl_create), or NULL: in memory */
 } cdl_options;
 
 /* Fills *opts with the defaults (everything zero / NULL except the
@@ -171,7 +186,7 @@ cdl_status cdl_relation_size(cdl_engine* e, cdl_rel rel, uint64_t* n);
 cdl_status cdl_relation_export(cdl_engine* e, cdl_rel rel, uint32_t* const* cols, uint64_t cap,
                                uint64_t* n_written, int on_device);
 
-/* Per-kernel timing gathered while options.timing == 1: for kernel class
+/* Per-kernel timing gathered while options.timing != 0: for kernel class
  * idx (0..), its name, launches, summed device milliseconds and summed
  * algorithmic bytes.  CDL_E_INVALID when idx is past the last class. */
 cdl_status cdl_kernel_profile(cdl_engine* e, uint32_t idx, char* name, size_t name_cap,

@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
                 ("timing", ctypes.c_uint32), ("estimator", ctypes.c_int32),
                 ("hash_load", ctypes.c_double), ("radix_bits", ctypes.c_uint32),
                 ("log_path", ctypes.c_char_p), ("est_margin", ctypes.c_double),
-                ("n_instances", ctypes.c_uint32)]
+                ("n_instances", ctypes.c_uint32), ("retire", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("tune_cache", ctypes.c_char_p)]
 
 MLP_IN = 16
 MLP_PARAMS = 5313
@@ -195,12 +196,34 @@ class RunStats:
     iters_per_instance: list = field(default_factory=list)
 
 
+# kernel classes in cdl_kernel_profile order
+KERNEL_CLASSES = ("hash_build", "count_heads", "join_count", "scan", "join_write",
+                  "radix_upsweep", "radix_scatter", "diff_count", "diff_merge", "select",
+                  "misc", "estimator", "join_direct", "retire")
+
+
+def _timing_mask(timing):
+    """options.timing from False / True / an iterable of kernel class names."""
+    if timing is True:
+        return 1
+    if not timing:
+        return 0
+    m = 0
+    for name in timing:
+        m |= 1 << (1 + KERNEL_CLASSES.index(name))
+    return m
+
+
 class Engine:
-    """One engine on the current CUDA device and stream (cdl_create)."""
+    """One engine on the current CUDA device and stream (cdl_create).
+
+    timing: False, True (every kernel class) or an iterable of class names
+    from KERNEL_CLASSES (events wrap only those launches)."""
 
     def __init__(self, *, device=None, stream=None, mem_limit=0, max_iters=0, spin_limit=0,
                  timing=False, hash_load=0.5, radix_bits=8, torch_alloc=True, estimator=0,
-                 est_margin=1.0, est_params=None, n_instances=0):
+                 est_margin=1.0, est_params=None, n_instances=0, retire=True, autotune=0,
+                 tune_cache=None):
         torch = _torch()
         L = lib()
         self._L = L
@@ -216,12 +239,15 @@ class Engine:
         opts.mem_limit = mem_limit
         opts.max_iters = max_iters
         opts.spin_limit = spin_limit
-        opts.timing = 1 if timing else 0
+        opts.timing = _timing_mask(timing)
         opts.hash_load = hash_load
         opts.radix_bits = radix_bits
         opts.estimator = estimator
         opts.est_margin = est_margin
         opts.n_instances = n_instances
+        opts.retire = 0 if retire else -1
+        opts.autotune = autotune
+        opts.tune_cache = os.fsencode(tune_cache) if tune_cache else None
         self.n_instances = n_instances
         self._opts = opts
         h = ctypes.c_void_p()

@@ -129,56 +129,66 @@ __device__ __forceinline__ uint64_t count_le_global(const ColsIn& F, uint64_t lo
   return lo;
 }
 
+// Persistent over tiles (grid = resident blocks): a tile without New tuples
+// costs one store, so a round whose few new tuples meet a large Full does
+// not pay one block launch per Full tile.
 template <int K>
 __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t nF, uint64_t nU,
                                                    const uint64_t* __restrict__ splits,
                                                    uint32_t* __restrict__ corank,
-                                                   uint32_t* __restrict__ tile_cnt) {
+                                                   uint32_t* __restrict__ tile_cnt,
+                                                   uint64_t ntiles) {
   extern __shared__ uint32_t s[];  // K x kDTile: the Full slice of a dense tile
   __shared__ uint32_t red[kDT / 32 + 1];
-  const uint64_t tile = blockIdx.x;
-  const uint64_t d0 = tile * kDTile;
-  const uint64_t d1 = d0 + kDTile < nF + nU ? d0 + kDTile : nF + nU;
-  const uint64_t a0 = splits[tile], a1 = splits[tile + 1];
-  const uint64_t b0 = d0 - a0, b1 = d1 - a1;
-  const uint32_t na = (uint32_t)(a1 - a0), nb = (uint32_t)(b1 - b0);
-  const bool dense = (uint64_t)nb * 16 >= na;
-  if (dense) {
-    for (uint32_t i = threadIdx.x; i < na; i += kDT) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) s[k * kDTile + i] = __ldg(F.c[k] + a0 + i);
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t d0 = tile * kDTile;
+    const uint64_t d1 = d0 + kDTile < nF + nU ? d0 + kDTile : nF + nU;
+    const uint64_t a0 = splits[tile], a1 = splits[tile + 1];
+    const uint64_t b0 = d0 - a0, b1 = d1 - a1;
+    const uint32_t na = (uint32_t)(a1 - a0), nb = (uint32_t)(b1 - b0);
+    if (nb == 0) {  // uniform over the block
+      if (threadIdx.x == 0) tile_cnt[tile] = 0;
+      continue;
     }
-    __syncthreads();
-  }
-  uint32_t cnt = 0;
-  for (uint64_t j = b0 + threadIdx.x; j < b1; j += kDT) {
-    uint32_t v[K];
+    const bool dense = (uint64_t)nb * 16 >= na;
+    if (dense) {
+      for (uint32_t i = threadIdx.x; i < na; i += kDT) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = __ldg(U.c[k] + j);
-    bool rep = j > 0 && eq_at<K>(U, j - 1, v);
-    uint32_t p = 0;
-    if (!rep) {
-      // the Full tuple just before v in merged order is F[a0 + p - 1]
-      p = dense ? count_le_smem<K>(s, na, v) : (uint32_t)(count_le_global<K>(F, a0, a1, v) - a0);
-      if (p > 0) {
-        if (dense) {
-          bool e = true;
-#pragma unroll
-          for (int k = 0; k < K; ++k) e &= s[k * kDTile + p - 1] == v[k];
-          rep = e;
-        } else {
-          rep = eq_at<K>(F, a0 + p - 1, v);
-        }
-      } else {
-        rep = a0 > 0 && eq_at<K>(F, a0 - 1, v);
+        for (int k = 0; k < K; ++k) s[k * kDTile + i] = __ldg(F.c[k] + a0 + i);
       }
+      __syncthreads();
     }
-    corank[j] = rep ? kRepeat : p;
-    cnt += rep ? 0u : 1u;
+    uint32_t cnt = 0;
+    for (uint64_t j = b0 + threadIdx.x; j < b1; j += kDT) {
+      uint32_t v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = __ldg(U.c[k] + j);
+      bool rep = j > 0 && eq_at<K>(U, j - 1, v);
+      uint32_t p = 0;
+      if (!rep) {
+        // the Full tuple just before v in merged order is F[a0 + p - 1]
+        p = dense ? count_le_smem<K>(s, na, v) : (uint32_t)(count_le_global<K>(F, a0, a1, v) - a0);
+        if (p > 0) {
+          if (dense) {
+            bool e = true;
+#pragma unroll
+            for (int k = 0; k < K; ++k) e &= s[k * kDTile + p - 1] == v[k];
+            rep = e;
+          } else {
+            rep = eq_at<K>(F, a0 + p - 1, v);
+          }
+        } else {
+          rep = a0 > 0 && eq_at<K>(F, a0 - 1, v);
+        }
+      }
+      corank[j] = rep ? kRepeat : p;
+      cnt += rep ? 0u : 1u;
+    }
+    uint32_t tot;
+    block_exclusive_sum<kDT, uint32_t>(cnt, red, &tot);
+    if (threadIdx.x == 0) tile_cnt[tile] = tot;
+    __syncthreads();  // the next tile reuses s and red
   }
-  uint32_t tot;
-  block_exclusive_sum<kDT, uint32_t>(cnt, red, &tot);
-  if (threadIdx.x == 0) tile_cnt[tile] = tot;
 }
 
 // shift table index with one padding word per 32 (blocked scans stay
@@ -297,16 +307,27 @@ cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, u
   w += up256((n_fresh ? n_fresh : 1) * 4);
   void* scan_ws = w;
   const size_t smem_count = sizeof(uint32_t) * K * kDTile;
-  cudaError_t e = cudaFuncSetAttribute(k_count_new<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_count);
-  if (e != cudaSuccess) return e;
+  static int resident = 0;  // blocks of k_count_new<K> the whole GPU holds at once
+  cudaError_t e = cudaSuccess;
+  if (!resident) {
+    e = cudaFuncSetAttribute(k_count_new<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_count);
+    int per_sm = 0, dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_new<K>, kDT, smem_count);
+    if (e != cudaSuccess) return e;
+    resident = (per_sm > 0 ? per_sm : 1) * sms;
+  }
+  const uint64_t count_grid = tiles < (uint64_t)resident ? tiles : (uint64_t)resident;
   {
     // New read, co-ranks written; Full sectors are read only where touched
     ProfScope p(c, kDiffCount, (4.0 * K + 4.0) * n_fresh);
     k_merge_splits<K><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, c.st>>>(full, n_full, fresh,
                                                                              n_fresh, splits, tiles);
-    k_count_new<K><<<(unsigned)tiles, kDT, smem_count, c.st>>>(full, fresh, n_full, n_fresh, splits,
-                                                               corank, cnt);
+    k_count_new<K><<<(unsigned)count_grid, kDT, smem_count, c.st>>>(full, fresh, n_full, n_fresh,
+                                                                     splits, corank, cnt, tiles);
   }
   e = exclusive_scan(c, cnt, tiles, pre, d_ndelta, scan_ws);
   if (e != cudaSuccess) return e;

@@ -30,6 +30,7 @@
 
 #include "../../include/cdl.h"
 #include "kernels.h"
+#include "tuner.h"
 
 using namespace cdl;
 
@@ -252,6 +253,10 @@ struct Relation {
   uint64_t fresh_ub = 0;
   uint32_t bound[kMaxK] = {0, 0, 0, 0};  // every value of column k is <= bound[k]
   uint64_t version[2] = {1, 1};
+  // batched runs: the rows of instances that reached their fixpoint leave
+  // full for this buffer (instance i: ret_cnt[i] rows from ret_off[i])
+  DCols retired;
+  std::vector<uint64_t> ret_off, ret_cnt;
 };
 
 struct Term {
@@ -280,6 +285,8 @@ struct Index {
   DBuf table;
   uint64_t slots = 0;
   uint64_t distinct = 0;  // distinct keys
+  std::string tkey;       // tuner decision of the load factor, if any
+  int tcand = 0;
 };
 
 // A table the join chain reads: columns hold the listed variables.
@@ -326,6 +333,7 @@ struct cdl_engine {
   std::vector<std::unique_ptr<Index>> cache;
   uint32_t radix_bits = 8;
   double hash_load = 0.5;
+  Tuner tuner;
   uint64_t joins = 0;
   // learned join-size estimator
   DBuf est_w, est_wb, est_io;  // FP32 and BF16 parameters; features + prediction
@@ -337,6 +345,8 @@ struct cdl_engine {
   std::vector<float> log_x, log_y;
   std::map<std::tuple<size_t, size_t, size_t>, uint64_t> prev_out;
   DBuf inst_last;  // batched runs: last round each instance derived a tuple
+  std::vector<uint64_t> h_inst;
+  std::vector<uint8_t> inst_live, inst_conv;  // rows still in full; fixpoint reached
   bool est_ready() const { return opt.estimator >= 1 && est_weights; }
 
   cdl_status install_weights(const float* host) {
@@ -478,15 +488,30 @@ struct cdl_engine {
   // Sorts d (n rows) lexicographically in place; bits[k] bounds column k.
   cdl_status sort_cols(DCols& d, const uint32_t* bits) {
     if (d.n <= 1) return CDL_OK;
-    RadixPlan plan = make_radix_plan(d.k, bits, radix_bits);
+    // tuner candidates: bit 0 the other digit width, bit 1 blocks of 256
+    int cand = 0;
+    bool measure = false;
+    std::string key;
+    if (tuner.mode && d.n >= (1u << 14)) {
+      uint32_t total = 0;
+      for (uint32_t k = 0; k < d.k; ++k) total += bits[k];
+      key = "sort.k" + std::to_string(d.k) + ".b" + std::to_string(total) + ".n" +
+            std::to_string(bits_of(d.n));
+      cand = tuner.choose(key, 4, &measure);
+    }
+    const uint32_t digit = (cand & 1) ? (radix_bits == 8 ? 10 : 8) : radix_bits;
+    RadixPlan plan = make_radix_plan(d.k, bits, digit, (cand & 2) ? 256 : 512);
     if (plan.npass == 0) return CDL_OK;
     DCols alt;
     if (!alloc_cols(alt, d.k, d.n)) return fail(CDL_E_NOMEM, "sort buffer");
-    DBuf ws = alloc(radix_workspace(d.n, plan.bits));
+    DBuf ws = alloc(radix_workspace(d.n, plan.bits, plan.threads));
     if (!ws.p) return fail(CDL_E_NOMEM, "sort workspace");
     bool in_b = false;
+    Tuner::Probe pr;
+    if (measure) pr = tuner.start(key, cand, (double)d.n, st);
     cudaError_t e = radix_sort(ctx, plan, d.out(), alt.out(), d.n, ws.p, &in_b);
     if (e != cudaSuccess) return cuda_fail(e, "radix_sort");
+    if (measure) tuner.stop(pr, st);
     if (in_b) {
       alt.n = d.n;
       std::swap(d, alt);
@@ -557,7 +582,15 @@ struct cdl_engine {
     cdl_status r = fetch(kSlotScratch, 1);
     if (r != CDL_OK) return r;
     ix->distinct = h_ctl[kSlotScratch];
-    ix->slots = table_slots(ix->distinct, hash_load);
+    double load = hash_load;
+    if (tuner.mode && ix->distinct >= 4096) {  // candidates: the configured load, 0.6, 0.7, 0.8
+      static const double kLoads[4] = {0.0, 0.6, 0.7, 0.8};
+      bool unused;
+      ix->tkey = "load.n" + std::to_string(bits_of(ix->distinct));
+      ix->tcand = tuner.choose(ix->tkey, 4, &unused);
+      if (ix->tcand) load = kLoads[ix->tcand];
+    }
+    ix->slots = table_slots(ix->distinct, load);
     ix->table = alloc(ix->slots * sizeof(Slot));
     if (!ix->table.p) return fail(CDL_E_NOMEM, "hash table");
     e = hash_build(ctx, k0, k1, s.n, static_cast<Slot*>(ix->table.p), ix->slots);
@@ -988,9 +1021,17 @@ struct cdl_engine {
       DBuf off = alloc(std::max<uint64_t>(P.n, 1) * 8);
       DBuf ws = alloc(join_count_workspace(P.n));
       if (!off.p || !ws.p) return fail(CDL_E_NOMEM, "join offsets");
+      // the probe cost per row measures the index's load factor for the tuner
+      Tuner::Probe tp;
+      if (ix && !ix->tkey.empty() && tuner.mode == 2 && P.n >= 4096) {
+        auto& ts = tuner.table[ix->tkey];
+        if ((size_t)ix->tcand < ts.size() && ts[ix->tcand].n < Tuner::kTrials)
+          tp = tuner.start(ix->tkey, ix->tcand, (double)P.n, st);
+      }
       cudaError_t e = join_count_scan(ctx, js, static_cast<uint64_t*>(off.p), dslot(kSlotScratch),
                                       ws.p);
       if (e != cudaSuccess) return cuda_fail(e, "join count");
+      tuner.stop(tp, st);
       r = fetch(kSlotScratch, kSlotCursor + (uint32_t)rels.size() - kSlotScratch);
       if (r != CDL_OK) return r;
       const uint64_t total = h_ctl[kSlotScratch];
@@ -1082,6 +1123,176 @@ struct cdl_engine {
     }
   }
 
+  // ------------------------------------------------------- batched runs
+  // Segment list for gather_segments; adjacent rows of one table coalesce.
+  struct Segs {
+    std::vector<uint64_t> off{0}, src;
+    void add(uint64_t from, uint64_t rows) {
+      if (!rows) return;
+      if (!src.empty()) {
+        const uint64_t last = src.back(), len = off.back() - off[off.size() - 2];
+        if ((last >> 63) == (from >> 63) && last + len == from) {
+          off.back() += rows;
+          return;
+        }
+      }
+      src.push_back(from);
+      off.push_back(off.back() + rows);
+    }
+    uint64_t total() const { return off.back(); }
+  };
+
+  cdl_status gather(const Segs& sg, uint32_t k, ColsIn a, ColsIn b, ColsOut out) {
+    if (sg.src.empty()) return CDL_OK;
+    DBuf d = alloc(8 * (sg.off.size() + sg.src.size()));
+    if (!d.p) return fail(CDL_E_NOMEM, "segment table");
+    uint64_t* doff = static_cast<uint64_t*>(d.p);
+    uint64_t* dsrc = doff + sg.off.size();
+    cudaError_t e = cudaMemcpyAsync(doff, sg.off.data(), 8 * sg.off.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dsrc, sg.src.data(), 8 * sg.src.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = gather_segments(ctx, k, a, b, doff, dsrc, (uint32_t)sg.src.size(), sg.total(), out);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host tables die here
+    return e == cudaSuccess ? CDL_OK : cuda_fail(e, "gather segments");
+  }
+
+  // Rows [bounds[i], bounds[i+1]) of each listed relation's full hold instance i.
+  cdl_status full_bounds(const std::vector<Relation*>& rs, std::vector<uint64_t>& hb) {
+    const uint32_t ni = opt.n_instances;
+    hb.assign((size_t)(ni + 1) * rs.size(), 0);
+    if (rs.empty()) return CDL_OK;
+    DBuf d = alloc(8 * hb.size());
+    if (!d.p) return fail(CDL_E_NOMEM, "instance bounds");
+    cudaError_t e = cudaSuccess;
+    for (size_t j = 0; j < rs.size() && e == cudaSuccess; ++j)
+      e = instance_bounds(ctx, rs[j]->full.c[0], rs[j]->full.n, ni,
+                          static_cast<uint64_t*>(d.p) + j * (ni + 1));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), d.p, 8 * hb.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? CDL_OK : cuda_fail(e, "instance bounds");
+  }
+
+  // An instance without a new tuple in any derived relation this round has
+  // reached its own fixpoint (instances share no tuples, and every rule
+  // joins its atoms on the instance column), so its rows can leave full:
+  // later rounds then merge only the instances still running.  The pass
+  // runs once the rows waiting to leave are at least 1/8 of full.
+  cdl_status retire(uint64_t round) {
+    const uint32_t ni = opt.n_instances;
+    cudaError_t e = cudaMemcpyAsync(h_inst.data(), inst_last.p, 8 * ni, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "instance marks");
+    bool any = false;
+    for (uint32_t i = 0; i < ni; ++i)
+      if (inst_live[i] && !inst_conv[i] && h_inst[i] != round) inst_conv[i] = any = true;
+    if (!any) return CDL_OK;
+    std::vector<Relation*> rs;
+    for (auto& r : rels)
+      if (r->idb && r->full.n) rs.push_back(r.get());
+    std::vector<uint64_t> hb;
+    cdl_status st_ = full_bounds(rs, hb);
+    if (st_ != CDL_OK) return st_;
+    uint64_t waiting = 0, rows = 0;
+    for (size_t j = 0; j < rs.size(); ++j) {
+      rows += rs[j]->full.n;
+      for (uint32_t i = 0; i < ni; ++i)
+        if (inst_live[i] && inst_conv[i]) waiting += hb[j * (ni + 1) + i + 1] - hb[j * (ni + 1) + i];
+    }
+    if (waiting * 8 < rows) return CDL_OK;
+    for (size_t j = 0; j < rs.size(); ++j) {
+      Relation& R = *rs[j];
+      const uint64_t* b = hb.data() + j * (ni + 1);
+      Segs keep, out;
+      for (uint32_t i = 0; i < ni; ++i) {
+        const uint64_t cnt = b[i + 1] - b[i];
+        if (!inst_live[i] || !cnt) continue;
+        if (inst_conv[i]) {
+          R.ret_off[i] = R.retired.n + out.total();
+          R.ret_cnt[i] = cnt;
+          out.add(b[i], cnt);
+        } else {
+          keep.add(b[i], cnt);
+        }
+      }
+      if (!out.total()) continue;
+      const uint64_t need = R.retired.n + out.total();
+      if (need > R.retired.cap) {
+        DCols grown;
+        if (!alloc_cols(grown, R.arity, std::max<uint64_t>(need, R.retired.cap + R.retired.cap / 2)))
+          return fail(CDL_E_NOMEM, "retired rows");
+        for (uint32_t k = 0; k < R.arity && R.retired.n; ++k) {
+          e = cudaMemcpyAsync(grown.c[k], R.retired.c[k], 4 * R.retired.n, cudaMemcpyDeviceToDevice, st);
+          if (e != cudaSuccess) return cuda_fail(e, "retired rows");
+        }
+        grown.n = R.retired.n;
+        R.retired = std::move(grown);
+      }
+      ColsOut tail = R.retired.out();
+      for (uint32_t k = 0; k < R.arity; ++k) tail.c[k] += R.retired.n;
+      st_ = gather(out, R.arity, R.full.in(), R.full.in(), tail);
+      if (st_ != CDL_OK) return st_;
+      R.retired.n = need;
+      DCols kept;
+      if (!alloc_cols(kept, R.arity, keep.total())) return fail(CDL_E_NOMEM, "kept rows");
+      st_ = gather(keep, R.arity, R.full.in(), R.full.in(), kept.out());
+      if (st_ != CDL_OK) return st_;
+      kept.n = keep.total();
+      R.full = std::move(kept);
+      R.version[kFull]++;
+    }
+    for (uint32_t i = 0; i < ni; ++i)
+      if (inst_conv[i]) inst_live[i] = 0;
+    return CDL_OK;
+  }
+
+  // Puts retired rows back: full becomes every instance's rows in instance
+  // order, the lexicographic order of the whole relation.
+  cdl_status assemble() {
+    const uint32_t ni = opt.n_instances;
+    std::vector<Relation*> rs;
+    for (auto& r : rels)
+      if (r->idb && r->retired.n) rs.push_back(r.get());
+    std::vector<uint64_t> hb;
+    cdl_status st_ = full_bounds(rs, hb);
+    if (st_ != CDL_OK) return st_;
+    for (size_t j = 0; j < rs.size(); ++j) {
+      Relation& R = *rs[j];
+      const uint64_t* b = hb.data() + j * (ni + 1);
+      Segs all;
+      for (uint32_t i = 0; i < ni; ++i) {
+        if (R.ret_cnt[i])
+          all.add(R.ret_off[i] | (1ull << 63), R.ret_cnt[i]);
+        else
+          all.add(b[i], b[i + 1] - b[i]);
+      }
+      DCols whole;
+      if (!alloc_cols(whole, R.arity, all.total())) return fail(CDL_E_NOMEM, "assembled relation");
+      st_ = gather(all, R.arity, R.full.in(), R.retired.in(), whole.out());
+      if (st_ != CDL_OK) return st_;
+      whole.n = all.total();
+      R.full = std::move(whole);
+      R.retired.clear();
+      R.version[kFull]++;
+    }
+    return CDL_OK;
+  }
+
+  // Batched runs: column 0 of every atom is one variable of the rule (the
+  // instance), and loaded instance ids are below n_instances.
+  cdl_status check_batched() {
+    for (const RuleR& rule : rules) {
+      const Term& h = rule.head.t.empty() ? Term{true, 0} : rule.head.t[0];
+      bool ok = !h.is_const;
+      for (const AtomR& a : rule.body) ok &= !a.t.empty() && !a.t[0].is_const && a.t[0].v == h.v;
+      if (!ok) return fail(CDL_E_INVALID, "batched rules must share the instance variable in column 0");
+    }
+    for (auto& r : rels)
+      if (r->arity == 0 || (r->full.n && r->bound[0] >= opt.n_instances))
+        return fail(CDL_E_VALUE, "relation " + r->name + " holds an instance id >= n_instances");
+    return CDL_OK;
+  }
+
   cdl_status run(cdl_stats* stats) {
     if (ran) return fail(CDL_E_STATE, "cdl_run was already called");
     ran = true;
@@ -1100,10 +1311,19 @@ struct cdl_engine {
     const uint32_t nr = (uint32_t)rels.size();
     est_pred = est_over = 0;
     if (opt.n_instances) {
+      cdl_status c = check_batched();
+      if (c != CDL_OK) return c;
       inst_last = alloc(sizeof(uint64_t) * opt.n_instances);
       if (!inst_last.p) return fail(CDL_E_NOMEM, "instance marks");
       if (cudaMemsetAsync(inst_last.p, 0, sizeof(uint64_t) * opt.n_instances, st) != cudaSuccess)
         return fail(CDL_E_CUDA, "instance marks");
+      h_inst.assign(opt.n_instances, 0);
+      inst_live.assign(opt.n_instances, 1);
+      inst_conv.assign(opt.n_instances, 0);
+      for (auto& r : rels) {
+        r->ret_off.assign(opt.n_instances, 0);
+        r->ret_cnt.assign(opt.n_instances, 0);
+      }
     }
     for (uint64_t round = 1; status == CDL_OK; ++round) {
       cur_round = round;
@@ -1166,7 +1386,12 @@ struct cdl_engine {
         }
       }
       if (status != CDL_OK) break;
+      if (opt.n_instances && new_total && opt.retire >= 0) {
+        status = retire(round);
+        if (status != CDL_OK) break;
+      }
       evict_stale();
+      tuner.resolve();  // the stream was synchronised by the fetches above
       rounds = round;
       per_round.push_back(new_total);
       if (new_total == 0) break;
@@ -1176,6 +1401,10 @@ struct cdl_engine {
         break;
       }
     }
+    if (opt.n_instances && status == CDL_OK) status = assemble();
+    tuner.resolve();
+    if (tuner.mode == 2 && !tuner.save() && status == CDL_OK)
+      status = fail(CDL_E_INVALID, "cannot write the tuner file");
     cudaEventRecord(t1, st);
     cudaEventSynchronize(t1);
     float ms = 0.f;
@@ -1278,7 +1507,12 @@ cdl_status cdl_create(const cdl_options* opts, cdl_engine** out) {
   e->pool.limit = e->opt.mem_limit;
   e->hash_load = (e->opt.hash_load > 0 && e->opt.hash_load <= 0.9) ? e->opt.hash_load : 0.5;
   e->radix_bits = e->opt.radix_bits == 10 ? 10 : 8;
+  e->tuner.mode = e->opt.autotune < 0 ? 0 : (e->opt.autotune > 2 ? 2 : e->opt.autotune);
+  e->tuner.path = e->opt.tune_cache ? e->opt.tune_cache : "";
+  e->opt.tune_cache = nullptr;  // the engine keeps its own copy of the path
+  if (e->tuner.mode) e->tuner.load();
   e->prof.on = e->opt.timing != 0;
+  e->prof.mask = e->opt.timing == 1 ? ~0u : e->opt.timing >> 1;
   e->est_margin = e->opt.est_margin != 0.0 ? e->opt.est_margin : 1.0;
   if ((e->opt.alloc == nullptr) != (e->opt.free == nullptr)) return CDL_E_INVALID;
   e->ctl = e->alloc(kCtlSlots * sizeof(uint64_t));

@@ -27,12 +27,14 @@ enum KernelClass : int {
   kMisc,
   kMlp,
   kJoinDirect,
+  kRetire,
   kNumClasses
 };
 const char* kernel_class_name(int c);
 
 struct Profiler {
   bool on = false;
+  uint32_t mask = ~0u;  // kernel classes timed while on
   struct Rec {
     int cls;
     cudaEvent_t a, b;
@@ -135,6 +137,7 @@ cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_
 struct RadixPlan {
   uint32_t k = 0;
   uint32_t bits = 8;
+  uint32_t threads = 512;  // block size of the upsweep and scatter passes (512 or 256)
   uint32_t npass = 0;
   struct Pass {
     uint32_t sh[kMaxK], mask[kMaxK], dsh[kMaxK];
@@ -142,8 +145,9 @@ struct RadixPlan {
   std::vector<Pass> pass;
 };
 // col_bits[k]: significant bits of column k (all values < 2^col_bits[k]).
-RadixPlan make_radix_plan(uint32_t k, const uint32_t* col_bits, uint32_t digit_bits);
-size_t radix_workspace(uint64_t n, uint32_t digit_bits);
+RadixPlan make_radix_plan(uint32_t k, const uint32_t* col_bits, uint32_t digit_bits,
+                          uint32_t threads = 512);
+size_t radix_workspace(uint64_t n, uint32_t digit_bits, uint32_t threads = 512);
 // Sorts (a, n rows) using b as the alternate buffer; returns in *in_b
 // whether the result ended in b.
 cudaError_t radix_sort(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t n, void* ws,
@@ -183,6 +187,16 @@ cudaError_t select_project(Ctx& c, const SelectSpec& s, ColsOut out, uint64_t* d
 // sorted instance column inst (n rows).
 cudaError_t mark_instances(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,
                            uint64_t* last_round, uint64_t round);
+// bounds[i] (i = 0..n_instances) = first row of the sorted column inst whose
+// value is >= i: instance i occupies rows [bounds[i], bounds[i + 1]).
+cudaError_t instance_bounds(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,
+                            uint64_t* bounds);
+// Concatenates nseg row segments of tables a and b (k columns) into out:
+// segment s fills out rows [out_off[s], out_off[s + 1]) (out_off has nseg + 1
+// entries, out_off[nseg] = total) from row src[s] of a, or of b when bit 63
+// of src[s] is set.  All pointers are device pointers.
+cudaError_t gather_segments(Ctx& c, uint32_t k, ColsIn a, ColsIn b, const uint64_t* out_off,
+                            const uint64_t* src, uint32_t nseg, uint64_t total, ColsOut out);
 
 // Reserved-value check and column maxima of loaded data.
 cudaError_t check_values(Ctx& c, ColsIn in, uint32_t k, uint64_t n, uint32_t* d_max);

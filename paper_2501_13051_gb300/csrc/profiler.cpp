@@ -7,7 +7,7 @@ const char* kernel_class_name(int c) {
   static const char* names[kNumClasses] = {
       "hash_build", "count_heads", "join_count", "scan",      "join_write", "radix_upsweep",
       "radix_scatter", "diff_count", "diff_merge", "select", "misc",
-      "estimator", "join_direct"};
+      "estimator", "join_direct", "retire"};
   return (c >= 0 && c < kNumClasses) ? names[c] : "?";
 }
 
@@ -24,7 +24,7 @@ cudaEvent_t Profiler::get() {
 
 void Profiler::begin(int cls, cudaStream_t st) {
   ++total_launches;
-  if (!on) return;
+  if (!on || !(mask >> cls & 1u)) return;
   Rec r{cls, get(), get(), 0.0};
   cudaEventRecord(r.a, st);
   open.push_back(r);
@@ -32,7 +32,7 @@ void Profiler::begin(int cls, cudaStream_t st) {
 
 void Profiler::end(int cls, double algo_bytes, cudaStream_t st) {
   total_bytes += algo_bytes;
-  if (!on) return;
+  if (!on || !(mask >> cls & 1u)) return;
   for (auto it = open.rbegin(); it != open.rend(); ++it) {
     if (it->cls == cls && it->bytes == 0.0) {
       cudaEventRecord(it->b, st);
@@ -44,7 +44,7 @@ void Profiler::end(int cls, double algo_bytes, cudaStream_t st) {
 
 void Profiler::add_bytes(int cls, double b) {
   total_bytes += b;
-  if (!on) return;
+  if (!on || !(mask >> cls & 1u)) return;
   for (auto it = open.rbegin(); it != open.rend(); ++it) {
     if (it->cls == cls) {
       it->bytes += b;

@@ -85,7 +85,85 @@ __global__ void k_mark_instances(const uint32_t* __restrict__ inst, uint64_t n,
   if ((i == 0 || __ldg(inst + i - 1) != v) && v < n_instances) last_round[v] = round;
 }
 
+// bounds[i] = the first row whose instance id (column 0, sorted) is >= i,
+// for i in [0, n_instances].
+__global__ void k_instance_bounds(const uint32_t* __restrict__ inst, uint64_t n,
+                                  uint32_t n_instances, uint64_t* __restrict__ bounds) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n_instances) return;
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if ((uint64_t)__ldg(inst + mid) < i)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  bounds[i] = lo;
+}
+
+// Output row j of segment s (out_off[s] <= j < out_off[s + 1]) copies row
+// src[s] + (j - out_off[s]) of table a, or of table b when bit 63 of src[s]
+// is set.  Consecutive rows of a segment are consecutive source rows, so
+// reads and writes stay coalesced.
+constexpr int kGT = 256;
+constexpr int kGItems = 8;
+constexpr uint32_t kGSmem = 2048;  // segment offsets held in shared memory
+
+template <bool SMEM>
+__global__ void __launch_bounds__(kGT) k_gather_segments(ColsIn a, ColsIn b, uint32_t k,
+                                                         const uint64_t* __restrict__ out_off,
+                                                         const uint64_t* __restrict__ src,
+                                                         uint32_t nseg, uint64_t total,
+                                                         ColsOut out) {
+  __shared__ uint64_t s_off[SMEM ? kGSmem + 1 : 1];
+  if (SMEM) {
+    for (uint32_t i = threadIdx.x; i <= nseg; i += kGT) s_off[i] = out_off[i];
+    __syncthreads();
+  }
+  const uint64_t base = (uint64_t)blockIdx.x * kGT * kGItems;
+  for (int it = 0; it < kGItems; ++it) {
+    const uint64_t j = base + (uint64_t)it * kGT + threadIdx.x;
+    if (j >= total) break;
+    uint32_t lo = 0, hi = nseg;  // the last segment whose start is <= j
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      const uint64_t o = SMEM ? s_off[mid] : __ldg(out_off + mid);
+      if (o <= j)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const uint64_t start = SMEM ? s_off[lo] : __ldg(out_off + lo);
+    const uint64_t sv = __ldg(src + lo);
+    const uint64_t row = (sv & ~(1ull << 63)) + (j - start);
+    const ColsIn& t = (sv >> 63) ? b : a;
+    for (uint32_t c = 0; c < k; ++c) out.c[c][j] = __ldg(t.c[c] + row);
+  }
+}
+
 }  // namespace
+
+cudaError_t instance_bounds(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,
+                            uint64_t* bounds) {
+  ProfScope p(c, kRetire, 8.0 * (n_instances + 1));
+  k_instance_bounds<<<(n_instances + 256) / 256, 256, 0, c.st>>>(inst, n, n_instances, bounds);
+  return cudaGetLastError();
+}
+
+cudaError_t gather_segments(Ctx& c, uint32_t k, ColsIn a, ColsIn b, const uint64_t* out_off,
+                            const uint64_t* src, uint32_t nseg, uint64_t total, ColsOut out) {
+  if (total == 0 || nseg == 0) return cudaSuccess;
+  ProfScope p(c, kRetire, 8.0 * k * total);
+  const uint64_t blocks = (total + kGT * kGItems - 1) / (kGT * kGItems);
+  if (nseg <= kGSmem)
+    k_gather_segments<true><<<(unsigned)blocks, kGT, 0, c.st>>>(a, b, k, out_off, src, nseg, total,
+                                                                 out);
+  else
+    k_gather_segments<false><<<(unsigned)blocks, kGT, 0, c.st>>>(a, b, k, out_off, src, nseg,
+                                                                  total, out);
+  return cudaGetLastError();
+}
 
 cudaError_t mark_instances(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,
                            uint64_t* last_round, uint64_t round) {

@@ -5,7 +5,7 @@
 // `bits`-wide digits of that packed key from the least significant end, so a
 // relation over ids < 2^18 sorts in ceil(36 / 8) = 5 passes instead of 8.
 //
-// Each pass: (1) every tile of 4096 tuples counts its digits in shared
+// Each pass: (1) every tile of 4096 (or 2048) tuples counts its digits in shared
 // memory; (2) an exclusive scan over the digit-major [digit][tile] counts
 // gives every (digit, tile) run its global start; (3) every tile ranks its
 // tuples stably (warp-level match on the digit, warps in order) and writes
@@ -18,10 +18,9 @@ namespace cdl {
 
 namespace {
 
-constexpr int kRT = 512;
+// T threads per block (512 or 256, the tuner's choice) and kRItems tuples
+// per thread: a tile holds T * kRItems tuples.
 constexpr int kRItems = 8;
-constexpr int kRTile = kRT * kRItems;
-constexpr int kRW = kRT / 32;
 
 struct PassP {
   uint32_t sh[kMaxK], mask[kMaxK], dsh[kMaxK];
@@ -35,11 +34,12 @@ __device__ __forceinline__ uint32_t digit_of(const uint32_t (&v)[K], const PassP
   return d;
 }
 
-template <int K, int BITS>
-__global__ void __launch_bounds__(kRT) k_radix_upsweep(ColsIn in, uint64_t n, PassP p,
-                                                       uint32_t* __restrict__ tile_hist,
-                                                       uint64_t ntiles) {
+template <int K, int BITS, int T>
+__global__ void __launch_bounds__(T) k_radix_upsweep(ColsIn in, uint64_t n, PassP p,
+                                                     uint32_t* __restrict__ tile_hist,
+                                                     uint64_t ntiles) {
   constexpr int R = 1 << BITS;
+  constexpr int kRT = T, kRTile = T * kRItems;
   __shared__ uint32_t h[R];
   for (int i = threadIdx.x; i < R; i += kRT) h[i] = 0;
   __syncthreads();
@@ -60,11 +60,12 @@ __global__ void __launch_bounds__(kRT) k_radix_upsweep(ColsIn in, uint64_t n, Pa
   for (int i = threadIdx.x; i < R; i += kRT) tile_hist[(uint64_t)i * ntiles + blockIdx.x] = h[i];
 }
 
-template <int K, int BITS>
-__global__ void __launch_bounds__(kRT) k_radix_scatter(ColsIn in, ColsOut out, uint64_t n, PassP p,
-                                                       const uint64_t* __restrict__ off,
-                                                       uint64_t ntiles) {
+template <int K, int BITS, int T>
+__global__ void __launch_bounds__(T) k_radix_scatter(ColsIn in, ColsOut out, uint64_t n, PassP p,
+                                                     const uint64_t* __restrict__ off,
+                                                     uint64_t ntiles) {
   constexpr int R = 1 << BITS;
+  constexpr int kRT = T, kRTile = T * kRItems, kRW = T / 32;
   constexpr int DPT = (R + kRT - 1) / kRT;
   __shared__ uint32_t wh[kRW][R];  // per-warp digit counts, then per-warp offsets
   __shared__ uint32_t tstart[R];   // tile-local start of each digit's run
@@ -167,10 +168,11 @@ __global__ void k_column_max(ColsIn in, uint32_t k, uint64_t n, uint32_t* d_max)
   }
 }
 
-template <int K, int BITS>
+template <int K, int BITS, int T>
 cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t n, void* ws,
                         bool* in_b) {
   constexpr int R = 1 << BITS;
+  constexpr int kRT = T, kRTile = T * kRItems;
   const uint64_t ntiles = (n + kRTile - 1) / kRTile;
   const uint64_t cells = (uint64_t)R * ntiles;
   uint32_t* hist = static_cast<uint32_t*>(ws);
@@ -178,7 +180,7 @@ cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uin
                                               ((cells * 4 + 255) & ~uint64_t(255)));
   void* scan_ws = reinterpret_cast<char*>(off) + ((cells * 8 + 255) & ~uint64_t(255));
   const size_t smem = sizeof(uint32_t) * K * kRTile;
-  cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<K, BITS>,
+  cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<K, BITS, T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   ColsOut src = a, dst = b;
@@ -199,15 +201,15 @@ cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uin
     if (!single) {
       {
         ProfScope ps(c, kRadixUpsweep, 4.0 * cols_used * n + 4.0 * cells);
-        k_radix_upsweep<K, BITS><<<(unsigned)ntiles, kRT, 0, c.st>>>(in, n, p, hist, ntiles);
+        k_radix_upsweep<K, BITS, T><<<(unsigned)ntiles, kRT, 0, c.st>>>(in, n, p, hist, ntiles);
       }
       e = exclusive_scan(c, hist, cells, off, nullptr, scan_ws);
       if (e != cudaSuccess) return e;
     }
     {
       ProfScope ps(c, kRadixScatter, 8.0 * K * n);
-      k_radix_scatter<K, BITS><<<(unsigned)ntiles, kRT, smem, c.st>>>(in, dst, n, p,
-                                                                     single ? nullptr : off, ntiles);
+      k_radix_scatter<K, BITS, T><<<(unsigned)ntiles, kRT, smem, c.st>>>(
+          in, dst, n, p, single ? nullptr : off, ntiles);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -221,19 +223,26 @@ cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uin
 template <int K>
 cudaError_t sort_k(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t n, void* ws,
                    bool* in_b) {
+  const bool wide = plan.threads == 512;
   switch (plan.bits) {
-    case 8: return sort_passes<K, 8>(c, plan, a, b, n, ws, in_b);
-    case 10: return sort_passes<K, 10>(c, plan, a, b, n, ws, in_b);
+    case 8:
+      return wide ? sort_passes<K, 8, 512>(c, plan, a, b, n, ws, in_b)
+                  : sort_passes<K, 8, 256>(c, plan, a, b, n, ws, in_b);
+    case 10:
+      return wide ? sort_passes<K, 10, 512>(c, plan, a, b, n, ws, in_b)
+                  : sort_passes<K, 10, 256>(c, plan, a, b, n, ws, in_b);
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-RadixPlan make_radix_plan(uint32_t k, const uint32_t* col_bits, uint32_t digit_bits) {
+RadixPlan make_radix_plan(uint32_t k, const uint32_t* col_bits, uint32_t digit_bits,
+                          uint32_t threads) {
   RadixPlan pl;
   pl.k = k;
   pl.bits = (digit_bits == 10) ? 10 : 8;
+  pl.threads = threads == 256 ? 256 : 512;
   uint32_t pos[kMaxK] = {0, 0, 0, 0};
   uint32_t total = 0;
   for (int c = (int)k - 1; c >= 0; --c) {
@@ -258,9 +267,10 @@ RadixPlan make_radix_plan(uint32_t k, const uint32_t* col_bits, uint32_t digit_b
   return pl;
 }
 
-size_t radix_workspace(uint64_t n, uint32_t digit_bits) {
+size_t radix_workspace(uint64_t n, uint32_t digit_bits, uint32_t threads) {
   const uint64_t R = 1ull << (digit_bits == 10 ? 10 : 8);
-  const uint64_t ntiles = (n + kRTile - 1) / kRTile;
+  const uint64_t tile = (threads == 256 ? 256 : 512) * kRItems;
+  const uint64_t ntiles = (n + tile - 1) / tile;
   const uint64_t cells = R * ntiles;
   return ((cells * 4 + 255) & ~uint64_t(255)) + ((cells * 8 + 255) & ~uint64_t(255)) +
          scan_workspace(cells);

@@ -19,14 +19,19 @@ def cdl():
     return C
 
 
-@pytest.mark.parametrize("count,seed,lo,hi", [(12, 77, 50, 3000), (33, 78, 20, 800)])
-def test_batched_equals_each_instance(cdl, oracle_lib, count, seed, lo, hi):
+@pytest.mark.parametrize("count,seed,lo,hi,retire", [(12, 77, 50, 3000, True),
+                                                    (12, 77, 50, 3000, False),
+                                                    (33, 78, 20, 800, True)])
+def test_batched_equals_each_instance(cdl, oracle_lib, count, seed, lo, hi, retire):
     graphs, kinds = W.batched_instances(count, seed, lo, hi)
     prog = W.batched_program(graphs, kinds)
-    with cdl.Engine(n_instances=count) as e:
+    with cdl.Engine(n_instances=count, retire=retire, timing=True) as e:
         e.load_program(prog)
         st = e.run()
         rel = {"tc": e.export("tc_path"), "sg": e.export("sg")}
+        moved = {p["kernel"]: p["launches"] for p in e.kernel_profile()}.get("retire", 0)
+    # converged instances left the merged relations (and came back at the end)
+    assert (moved > 0) == retire
     whole = oracle_lib.run_program(prog)
     assert np.array_equal(rel["tc"], whole.relations["tc_path"])
     assert np.array_equal(rel["sg"], whole.relations["sg"])
@@ -57,3 +62,21 @@ def test_batched_with_estimator_is_exact(cdl, oracle_lib):
         got = e.export("tc_path")
     assert np.array_equal(got, oracle_lib.run_program(prog).relations["tc_path"])
     assert st.est_predictions > 0
+
+
+def test_batched_contract_is_checked(cdl):
+    graphs, kinds = W.batched_instances(4, 80, 20, 100)
+    prog = W.batched_program(graphs, kinds)
+    with cdl.Engine(n_instances=3) as e:  # instance 3 is out of range
+        e.load_program(prog)
+        with pytest.raises(cdl.CdlError) as ex:
+            e.run()
+        assert ex.value.name == "CDL_E_VALUE"
+    with cdl.Engine(n_instances=4) as e:  # a rule that ignores the instance column
+        e.relation("a", 3)
+        e.relation("b", 3)
+        e.load("a", np.array([[0, 1, 2]], dtype=np.uint32))
+        e.rule(("b", ["x", "x", "y"]), [("a", ["i", "x", "y"])])
+        with pytest.raises(cdl.CdlError) as ex:
+            e.run()
+        assert ex.value.name == "CDL_E_INVALID"
