@@ -55,19 +55,25 @@ WORKLOADS = {
                             desc="transitive closure on a directed Erdos-Renyi graph, "
                                  "1000 nodes, 1500 edges",
                             sample=dict(kind="tc", n=1000, m=1500, seed=1)),
-    "points-to": dict(kind="pt", scale=1 / 32, seed=3,
+    "points-to": dict(kind="pt", scale=1 / 512, seed=3, learned=True,
                       desc="points-to analysis (valueFlow / memoryAlias / valueAlias), "
-                           "Zipf(1.1) endpoints, 2M vars / 4M assign / 1M deref times scale",
-                      sample=dict(kind="pt", scale=1 / 1024, seed=3)),
-    "owl-rl-20m": dict(kind="owl", triples=20_000_000, seed=4,
+                           "Zipf(1.1) endpoints, 2M vars / 4M assign / 1M deref times scale; "
+                           "learned join-size estimator on, exact count pass as fallback",
+                      sample=dict(kind="pt", scale=1 / 1024, seed=3),
+                      train=dict(kind="pt", scale=1 / 1024, seed=103)),
+    "owl-rl-20m": dict(kind="owl", triples=20_000_000, seed=4, learned=True,
                        desc="OWL-2-RL-style rules over 20M synthetic triples, 5M entities, "
-                            "500 classes, 200 properties, 193 rule instances",
-                       sample=dict(kind="owl", triples=1_000_000, seed=4)),
-    "batched-512": dict(kind="batch", count=512, seed=5, lo=1e3, hi=5e5,
+                            "500 classes, 200 properties, 193 rule instances; learned "
+                            "join-size estimator on, exact count pass as fallback",
+                       sample=dict(kind="owl", triples=1_000_000, seed=4),
+                       train=dict(kind="owl", triples=2_000_000, seed=104)),
+    "batched-512": dict(kind="batch", count=512, seed=5, lo=1e3, hi=5e5, learned=True, tune=True,
                         desc="512 independent fixpoints in one batched run (instance column "
                              "leading): TC on even, SG on odd instances, directed ER graphs "
-                             "with log-uniform 1e3..5e5 edges, mean out-degree 0.9",
-                        sample=dict(kind="batch", count=16, seed=5, lo=1e3, hi=2e4)),
+                             "with log-uniform 1e3..5e5 edges, mean out-degree 0.9; launch "
+                             "parameters from the autotuner, learned join-size estimator on",
+                        sample=dict(kind="batch", count=16, seed=5, lo=1e3, hi=2e4),
+                        train=dict(kind="batch", count=64, seed=105, lo=1e3, hi=5e5)),
 }
 METRIC = "derived tuples/s per fixpoint"
 
@@ -88,6 +94,24 @@ def make_program(spec, seed_offset=0, scale=None):
     if kind == "batch":
         return W.batched_program(*W.batched_instances(spec["count"], seed, spec["lo"], spec["hi"]))
     raise ValueError(kind)
+
+
+def train_estimator(spec, seed_offset=0):
+    """Logs every join of a run of the workload's training instance (another
+    seed, smaller), then trains the size network on the GPU with the
+    library's own kernels.  Returns (parameters, samples, seconds)."""
+    from paper_2501_13051_gb300 import cdl
+    t0 = time.time()
+    prog = make_program(spec["train"], seed_offset)
+    ninst = spec["train"]["count"] if spec["kind"] == "batch" else 0
+    with cdl.Engine(estimator=2, n_instances=ninst) as e:
+        e.load_program(prog)
+        e.run()
+        X, y = e.estimator_log()
+    with cdl.Engine() as t:
+        t.estimator_train(X, y, epochs=2000)
+        params = t.estimator_params()
+    return params, len(y), time.time() - t0
 
 
 def sequential_baseline(spec, seed_offset=0):
@@ -263,8 +287,29 @@ def bench_gb300(args, rank, world, dist):
         for r in prog.rules:
             e.rule(r.head, r.body, r.neq)
 
-    def step(timing):
-        with cdl.Engine(timing=timing, n_instances=ninst) as e:
+    # the form the workload names: autotuned launch parameters (tuning runs
+    # first, untimed) and / or the learned estimator (trained first, untimed)
+    form = {}
+    tune_dir = tempfile.mkdtemp(prefix="cdl_tune_")
+    if spec.get("tune"):
+        cache = os.path.join(tune_dir, "tune.txt")
+        for _ in range(6):
+            with cdl.Engine(n_instances=ninst, autotune=2, tune_cache=cache) as e:
+                declare(e)
+                for nm, cols in dev_edb.items():
+                    e.load(nm, cols)
+                rules(e)
+                e.run()
+        form.update(autotune=1, tune_cache=cache)
+    trained = None
+    if spec.get("learned"):
+        params, nsamp, tsec = train_estimator(spec, rank)
+        form.update(estimator=1, est_params=params)
+        trained = {"samples": nsamp, "seconds": round(tsec, 2),
+                   "instance": describe_sample(spec["train"], 0, 0).split(":")[0]}
+
+    def step(timing, plain=False):
+        with cdl.Engine(timing=timing, n_instances=ninst, **({} if plain else form)) as e:
             declare(e)
             for nm, cols in dev_edb.items():
                 e.load(nm, cols)
@@ -318,11 +363,27 @@ def bench_gb300(args, rank, world, dist):
     value = derived / secs
     per_step = st.derived_tuples
 
+    # ---- the plain exact form (no estimator, no tuner), timed the same way
+    plain = None
+    if form:
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record()
+        pd = 0
+        for i in range(args.steps):
+            if i:
+                flush.fill_(i & 0xFF)
+            pd += step(False, plain=True)[0].derived_tuples
+        p1.record()
+        torch.cuda.synchronize()
+        psecs = p0.elapsed_time(p1) * 1e-3
+        plain = {"tuples_per_s": pd / psecs, "ms_per_step": 1e3 * psecs / args.steps}
+
     # ---- end to end through the C ABI with host buffers
     pinned_in = {nm: [torch.from_numpy(c.view(np.int32)).pin_memory() for c in cols]
                  for nm, cols in host_cols.items()}
     sizes = {}
-    with cdl.Engine(n_instances=ninst) as e:
+    with cdl.Engine(n_instances=ninst, **form) as e:
         declare(e)
         for nm, cols in dev_edb.items():
             e.load(nm, cols)
@@ -333,7 +394,7 @@ def bench_gb300(args, rank, world, dist):
                        for _ in range(prog.arity[nm])] for nm in idb}
 
     def step_e2e():
-        with cdl.Engine(n_instances=ninst) as e:
+        with cdl.Engine(n_instances=ninst, **form) as e:
             declare(e)
             for nm, cols in pinned_in.items():
                 e.load(nm, cols)
@@ -385,6 +446,14 @@ def bench_gb300(args, rank, world, dist):
               "parallelism": f"replicas x{world}"}
     if spec["kind"] == "pt":
         config["scale"] = args.scale or spec["scale"]
+    if spec.get("learned"):
+        config["estimator"] = {"trained_on": trained, "predictions": int(st.est_predictions),
+                               "fallbacks": int(st.est_overflows)}
+    if spec.get("tune"):
+        config["autotune"] = "6 tuning runs (untimed), then the cached choices"
+    if plain is not None:
+        config["plain_exact"] = plain
+        config["form_over_plain_exact"] = value / plain["tuples_per_s"]
     if spec["kind"] == "batch":
         sd, ss = sequential_baseline(spec, seed_offset=rank)
         config["instances"] = spec["count"]

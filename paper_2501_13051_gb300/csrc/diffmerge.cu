@@ -151,10 +151,24 @@ __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t 
       continue;
     }
     const bool dense = (uint64_t)nb * 16 >= na;
-    if (dense) {
-      for (uint32_t i = threadIdx.x; i < na; i += kDT) {
+    if (dense) {  // stage the Full slice, eight loads per column in flight
+      constexpr int kS = 8;
+      for (uint32_t base = 0; base < na; base += kS * kDT) {
+        uint32_t v[kS][K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) s[k * kDTile + i] = __ldg(F.c[k] + a0 + i);
+        for (int u = 0; u < kS; ++u) {
+          const uint32_t i = base + u * kDT + threadIdx.x;
+#pragma unroll
+          for (int k = 0; k < K; ++k) v[u][k] = i < na ? __ldg(F.c[k] + a0 + i) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kS; ++u) {
+          const uint32_t i = base + u * kDT + threadIdx.x;
+          if (i < na) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) s[k * kDTile + i] = v[u][k];
+          }
+        }
       }
       __syncthreads();
     }
@@ -265,7 +279,7 @@ __global__ void __launch_bounds__(kDT) k_merge_write(ColsIn F, uint64_t nF, Cols
   }
   if (!merged) return;
   // the Full slice, four loads in flight per thread and column
-  constexpr int kU = 4;
+  constexpr int kU = 8;
   for (uint32_t base = 0; base < na; base += kU * kDT) {
     uint32_t v[kU][K];
 #pragma unroll

@@ -251,6 +251,7 @@ struct Relation {
   bool idb = false;
   DCols full, delta, fresh;
   uint64_t fresh_ub = 0;
+  bool fresh_overflow = false;  // a predicted join of this round claimed past fresh.cap
   uint32_t bound[kMaxK] = {0, 0, 0, 0};  // every value of column k is <= bound[k]
   uint64_t version[2] = {1, 1};
   // batched runs: the rows of instances that reached their fixpoint leave
@@ -308,10 +309,12 @@ struct Src {
 constexpr uint32_t kMaxRels = 1024;
 // control block slots (uint64): 0 error word, 1 scratch, 2 aux cursor,
 // 4 + r fresh cursor of relation r, 4 + kMaxRels + r delta size of r
-// 3 single-pass join size, 4 overflow flag, 8 + r fresh cursor of relation r,
+// 3 single-pass join size, 4 overflow flag, 5 overflow flag of the round's
+// deferred checks, 8 + r fresh cursor of relation r,
 // 8 + kMaxRels + r delta size of relation r
 constexpr uint32_t kSlotErr = 0, kSlotScratch = 1, kSlotAux = 2, kSlotDirTotal = 3,
-                   kSlotOverflow = 4, kSlotCursor = 8, kSlotDelta = 8 + kMaxRels,
+                   kSlotOverflow = 4, kSlotRoundOverflow = 5, kSlotCursor = 8,
+                   kSlotDelta = 8 + kMaxRels,
                    kCtlSlots = 8 + 2 * kMaxRels;
 constexpr int kEstFloats = 32;  // 16 features, the prediction, padding
 
@@ -344,6 +347,20 @@ struct cdl_engine {
   uint64_t cur_round = 0;
   std::vector<float> log_x, log_y;
   std::map<std::tuple<size_t, size_t, size_t>, uint64_t> prev_out;
+  // predicted joins that write a head relation leave their overflow check
+  // to the end of the round: their sizes land in join_sizes[i]
+  static constexpr uint32_t kMaxDeferred = 4096;
+  static constexpr double kDirectMaxTuples = double(1 << 24);
+  struct Deferred {
+    std::tuple<size_t, size_t, size_t> step;
+    uint32_t head = 0;  // relation the join appends to
+    float feat[kMlpIn];
+  };
+  std::vector<Deferred> deferred;
+  DBuf join_sizes;
+  DBuf heavy_buf;  // the single-pass join's list of long-range chunks
+  HeavyList heavy;
+  bool force_exact = false;  // rules are being redone without predictions
   DBuf inst_last;  // batched runs: last round each instance derived a tuple
   std::vector<uint64_t> h_inst;
   std::vector<uint8_t> inst_live, inst_conv;  // rows still in full; fixpoint reached
@@ -622,9 +639,12 @@ struct cdl_engine {
     uint64_t cap = std::max<uint64_t>(need, r.fresh.cap + r.fresh.cap / 2);
     if (cap < 1024) cap = 1024;
     if (!alloc_cols(nf, r.arity, cap)) return fail(CDL_E_NOMEM, "new-tuple buffer");
-    if (r.fresh.buf.p && r.fresh_ub) {
+    // rows past the old capacity were never written (a claim beyond the
+    // buffer marks the relation for an exact redo): copy only what exists
+    const uint64_t rows = std::min(r.fresh_ub, r.fresh.cap);
+    if (r.fresh.buf.p && rows) {
       for (uint32_t k = 0; k < r.arity; ++k) {
-        cudaError_t e = cudaMemcpyAsync(nf.c[k], r.fresh.c[k], r.fresh_ub * 4,
+        cudaError_t e = cudaMemcpyAsync(nf.c[k], r.fresh.c[k], rows * 4,
                                         cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "grow new-tuple buffer");
       }
@@ -747,7 +767,7 @@ struct cdl_engine {
     cdl_status r = ensure_fresh(H, base.n);
     if (r != CDL_OK) return r;
     cudaError_t e = select_project(ctx, sp, H.fresh.out(), dslot(kSlotCursor + rule.head.rel),
-                                   H.fresh.cap);
+                                   H.fresh.cap, soft_overflow());
     return e == cudaSuccess ? CDL_OK : cuda_fail(e, "copy rule");
   }
 
@@ -782,7 +802,7 @@ struct cdl_engine {
     cdl_status r = ensure_fresh(H, sp.n);
     if (r != CDL_OK) return r;
     cudaError_t e = select_project(ctx, sp, H.fresh.out(), dslot(kSlotCursor + rule.head.rel),
-                                   H.fresh.cap);
+                                   H.fresh.cap, soft_overflow());
     return e == cudaSuccess ? CDL_OK : cuda_fail(e, "project");
   }
 
@@ -956,64 +976,88 @@ struct cdl_engine {
         log_y.push_back((float)std::log2(1.0 + (double)size));
       };
       bool predicted = false;
-      if (feats && est_ready()) {
+      if (feats && est_ready() && !force_exact) {
         // single pass into a buffer sized by the prediction
         r = fetch(kSlotScratch, kSlotCursor + (uint32_t)rels.size() - kSlotScratch);
         if (r != CDL_OK) return r;
+        note_cursors();
+        if (last && rels[rule.head.rel]->fresh_overflow) return CDL_OK;  // redone exact
         const double want = std::exp2(std::min(40.0, (double)h_est[kMlpIn] + est_margin));
-        const uint64_t cap = std::max<uint64_t>(256, (uint64_t)std::ceil(want));
-        Relation* H = last ? rels[rule.head.rel].get() : nullptr;
-        const uint64_t cur0 = last ? h_ctl[kSlotCursor + rule.head.rel] : 0;
-        uint64_t* cursor = dslot(last ? kSlotCursor + rule.head.rel : kSlotAux);
-        bool room = true;
-        ColsOut out{};
-        uint64_t out_cap = 0;
-        if (last) {
-          H->fresh_ub = cur0;
-          room = ensure_fresh(*H, cap) == CDL_OK;
-          out = H->fresh.out();
-          out_cap = H->fresh.cap;
-        } else {
-          next.k = js.out_k;
-          room = alloc_cols(next.owned, next.k, cap);
-          out = next.owned.out();
-          out_cap = cap;
-        }
-        if (room) {
-          cudaError_t e = cudaMemsetAsync(dslot(kSlotDirTotal), 0, 16, st);  // total, overflow
-          if (e == cudaSuccess && !last) e = cudaMemsetAsync(cursor, 0, 8, st);
-          if (e == cudaSuccess)
-            e = join_direct(ctx, js, out, cursor, out_cap, dslot(kSlotDirTotal),
-                            reinterpret_cast<uint32_t*>(dslot(kSlotOverflow)));
-          if (e != cudaSuccess) return cuda_fail(e, "single-pass join");
-          r = fetch(kSlotDirTotal, 2);
-          if (r != CDL_OK) return r;
-          const uint64_t total = h_ctl[kSlotDirTotal];
-          if (h_ctl[kSlotOverflow] == 0) {
-            predicted = true;
+        // a large predicted join keeps the count pass: next to its write the
+        // count is cheap, while an overflow would cost the whole round
+        if (want <= kDirectMaxTuples) {
+          const uint64_t cap = std::max<uint64_t>(256, (uint64_t)std::ceil(want));
+          Relation* H = last ? rels[rule.head.rel].get() : nullptr;
+          const uint64_t cur0 = last ? h_ctl[kSlotCursor + rule.head.rel] : 0;
+          uint64_t* cursor = dslot(last ? kSlotCursor + rule.head.rel : kSlotAux);
+          bool room = true;
+          ColsOut out{};
+          uint64_t out_cap = 0;
+          if (last) {
+            H->fresh_ub = cur0;
+            room = ensure_fresh(*H, cap) == CDL_OK;
+            out = H->fresh.out();
+            out_cap = H->fresh.cap;
+          } else {
+            next.k = js.out_k;
+            room = alloc_cols(next.owned, next.k, cap);
+            out = next.owned.out();
+            out_cap = cap;
+          }
+          if (room && last && deferred.size() < kMaxDeferred) {
+            // no wait: the round's end reads the size and the overflow flag
+            const uint32_t di = (uint32_t)deferred.size();
+            cudaError_t e = cudaMemsetAsync(heavy.n, 0, 8, st);
+            if (e == cudaSuccess)
+              e = join_direct(ctx, js, out, cursor, out_cap, static_cast<uint64_t*>(join_sizes.p) + di,
+                              reinterpret_cast<uint32_t*>(dslot(kSlotRoundOverflow)), heavy);
+            if (e != cudaSuccess) return cuda_fail(e, "single-pass join");
+            Deferred d;
+            d.step = step_key;
+            d.head = rule.head.rel;
+            std::copy(h_est, h_est + kMlpIn, d.feat);
+            deferred.push_back(d);
             ++est_pred;
             ++joins;
-            log_sample(total);
-            if (last) return CDL_OK;
-            r = fetch(kSlotAux, 1);
-            if (r != CDL_OK) return r;
-            next.n = next.owned.n = h_ctl[kSlotAux];
-            for (uint32_t k = 0; k < next.k; ++k) next.c[k] = next.owned.c[k];
-            if (next.n == 0) return CDL_OK;
-            left = std::move(next);
-            continue;
+            return CDL_OK;
           }
-        }
-        // the prediction was too small: undo the claims, then the exact join
-        ++est_over;
-        if (last) {
-          h_ctl[kSlotScratch] = cur0;
-          cudaError_t e = cudaMemcpyAsync(cursor, h_ctl + kSlotScratch, 8, cudaMemcpyHostToDevice, st);
-          if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-          if (e != cudaSuccess) return cuda_fail(e, "cursor rollback");
-          H->fresh_ub = cur0;
-        } else {
-          next.owned.clear();
+          if (room) {
+            cudaError_t e = cudaMemsetAsync(dslot(kSlotDirTotal), 0, 16, st);  // total, overflow
+            if (e == cudaSuccess && !last) e = cudaMemsetAsync(cursor, 0, 8, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(heavy.n, 0, 8, st);
+            if (e == cudaSuccess)
+              e = join_direct(ctx, js, out, cursor, out_cap, dslot(kSlotDirTotal),
+                              reinterpret_cast<uint32_t*>(dslot(kSlotOverflow)), heavy);
+            if (e != cudaSuccess) return cuda_fail(e, "single-pass join");
+            r = fetch(kSlotDirTotal, 2);
+            if (r != CDL_OK) return r;
+            const uint64_t total = h_ctl[kSlotDirTotal];
+            if (h_ctl[kSlotOverflow] == 0) {
+              predicted = true;
+              ++est_pred;
+              ++joins;
+              log_sample(total);
+              if (last) return CDL_OK;
+              r = fetch(kSlotAux, 1);
+              if (r != CDL_OK) return r;
+              next.n = next.owned.n = h_ctl[kSlotAux];
+              for (uint32_t k = 0; k < next.k; ++k) next.c[k] = next.owned.c[k];
+              if (next.n == 0) return CDL_OK;
+              left = std::move(next);
+              continue;
+            }
+          }
+          // the prediction was too small: undo the claims, then the exact join
+          ++est_over;
+          if (last) {
+            h_ctl[kSlotScratch] = cur0;
+            cudaError_t e = cudaMemcpyAsync(cursor, h_ctl + kSlotScratch, 8, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(e, "cursor rollback");
+            H->fresh_ub = cur0;
+          } else {
+            next.owned.clear();
+          }
         }
       }
       (void)predicted;
@@ -1034,6 +1078,8 @@ struct cdl_engine {
       tuner.stop(tp, st);
       r = fetch(kSlotScratch, kSlotCursor + (uint32_t)rels.size() - kSlotScratch);
       if (r != CDL_OK) return r;
+      note_cursors();
+      if (last && !force_exact && rels[rule.head.rel]->fresh_overflow) return CDL_OK;
       const uint64_t total = h_ctl[kSlotScratch];
       ++joins;
       log_sample(total);
@@ -1076,6 +1122,8 @@ struct cdl_engine {
   }
 
   cdl_status eval_rule(const RuleR& rule, bool first_round) {
+    // a head relation already marked for an exact redo gains nothing more now
+    if (!force_exact && rels[rule.head.rel]->fresh_overflow) return CDL_OK;
     const size_t nb = rule.body.size();
     if (first_round) {
       if (nb == 1) return eval_copy(rule, kFull);
@@ -1293,6 +1341,89 @@ struct cdl_engine {
     return CDL_OK;
   }
 
+  // Where a head relation's buffer may already be overrun by a predicted join
+  // (whose check waits for the round's end), an appending selection reports
+  // running out of room in the round's overflow word, not as an error: the
+  // relation is then redone exact.
+  uint32_t* soft_overflow() {
+    return est_ready() && !force_exact ? reinterpret_cast<uint32_t*>(dslot(kSlotRoundOverflow))
+                                       : nullptr;
+  }
+
+  // A claim past a head relation's buffer (the cursor counts every claim)
+  // marks that relation's round for a redo; read after every cursor fetch.
+  void note_cursors() {
+    for (uint32_t i = 0; i < rels.size(); ++i) {
+      Relation& R = *rels[i];
+      if (R.idb && h_ctl[kSlotCursor + i] > R.fresh.cap) R.fresh_overflow = true;
+    }
+  }
+
+  // Every rule once; then the cursors (and the deferred joins' sizes) are
+  // read back.  A relation whose predicted joins claimed past its buffer has
+  // only appended to that buffer: its rules run again, exact, from an empty
+  // buffer; the other relations keep their tuples.
+  cdl_status eval_round(uint64_t round) {
+    const uint32_t nr = (uint32_t)rels.size();
+    deferred.clear();
+    force_exact = false;
+    cudaError_t e = cudaMemsetAsync(dslot(kSlotCursor), 0, 8 * nr, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dslot(kSlotRoundOverflow), 0, 8, st);
+    if (e == cudaSuccess && est_ready()) e = cudaMemsetAsync(join_sizes.p, 0, 8 * kMaxDeferred, st);
+    if (e != cudaSuccess) return cuda_fail(e, "round reset");
+    for (auto& r : rels) {
+      r->fresh_ub = 0;
+      r->fresh_overflow = false;
+    }
+    for (const RuleR& rule : rules) {
+      cdl_status s = eval_rule(rule, round == 1);
+      if (s != CDL_OK) return s;
+    }
+    cdl_status s = fetch(kSlotRoundOverflow, kSlotCursor + nr - kSlotRoundOverflow);
+    if (s != CDL_OK) return s;
+    note_cursors();
+    std::vector<bool> redo(nr, false);
+    bool any = false;
+    for (uint32_t i = 0; i < nr; ++i)
+      if (rels[i]->fresh_overflow) redo[i] = any = true;
+    if (!deferred.empty()) {  // exact sizes of the predicted joins
+      std::vector<uint64_t> sz(deferred.size());
+      e = cudaMemcpyAsync(sz.data(), join_sizes.p, 8 * sz.size(), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "join sizes");
+      for (size_t i = 0; i < deferred.size(); ++i) {
+        if (deferred[i].head < nr && redo[deferred[i].head]) continue;  // measured again
+        prev_out[deferred[i].step] = sz[i];
+        if (opt.estimator >= 2) {
+          log_x.insert(log_x.end(), deferred[i].feat, deferred[i].feat + kMlpIn);
+          log_y.push_back((float)std::log2(1.0 + (double)sz[i]));
+        }
+      }
+    }
+    if (!any) return CDL_OK;
+    force_exact = true;
+    for (uint32_t i = 0; i < nr; ++i)
+      if (redo[i]) {
+        ++est_over;
+        rels[i]->fresh_ub = 0;
+        rels[i]->fresh_overflow = false;
+        e = cudaMemsetAsync(dslot(kSlotCursor + i), 0, 8, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cursor reset");
+      }
+    for (const RuleR& rule : rules) {
+      if (!redo[rule.head.rel]) continue;
+      s = eval_rule(rule, round == 1);
+      if (s != CDL_OK) return s;
+    }
+    force_exact = false;
+    s = fetch(kSlotRoundOverflow, kSlotCursor + nr - kSlotRoundOverflow);
+    if (s != CDL_OK) return s;
+    for (uint32_t i = 0; i < nr; ++i)
+      if (redo[i] && h_ctl[kSlotCursor + i] > rels[i]->fresh.cap)
+        return fail(CDL_E_CAPACITY, "an exact join overflowed its buffer");
+    return CDL_OK;
+  }
+
   cdl_status run(cdl_stats* stats) {
     if (ran) return fail(CDL_E_STATE, "cdl_run was already called");
     ran = true;
@@ -1310,6 +1441,15 @@ struct cdl_engine {
     cdl_status status = CDL_OK;
     const uint32_t nr = (uint32_t)rels.size();
     est_pred = est_over = 0;
+    if (opt.estimator >= 1) {
+      constexpr uint64_t kHeavyCap = 1 << 20;  // chunks of 2048 outputs: 2^31 outputs
+      join_sizes = alloc(8 * kMaxDeferred);
+      heavy_buf = alloc(256 + sizeof(HeavyChunk) * kHeavyCap);
+      if (!join_sizes.p || !heavy_buf.p) return fail(CDL_E_NOMEM, "join sizes");
+      heavy.n = static_cast<uint64_t*>(heavy_buf.p);
+      heavy.e = reinterpret_cast<HeavyChunk*>(static_cast<char*>(heavy_buf.p) + 256);
+      heavy.cap = kHeavyCap;
+    }
     if (opt.n_instances) {
       cdl_status c = check_batched();
       if (c != CDL_OK) return c;
@@ -1327,18 +1467,8 @@ struct cdl_engine {
     }
     for (uint64_t round = 1; status == CDL_OK; ++round) {
       cur_round = round;
-      cudaError_t e = cudaMemsetAsync(dslot(kSlotCursor), 0, 8 * nr, st);
-      if (e != cudaSuccess) {
-        status = cuda_fail(e, "round reset");
-        break;
-      }
-      for (auto& r : rels) r->fresh_ub = 0;
-      for (const RuleR& rule : rules) {
-        status = eval_rule(rule, round == 1);
-        if (status != CDL_OK) break;
-      }
-      if (status != CDL_OK) break;
-      status = fetch(kSlotCursor, nr);
+      cudaError_t e = cudaSuccess;
+      status = eval_round(round);
       if (status != CDL_OK) break;
       for (uint32_t i = 0; i < nr; ++i) {
         Relation& R = *rels[i];

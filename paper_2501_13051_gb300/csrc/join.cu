@@ -229,11 +229,56 @@ cudaError_t join_count_scan(Ctx& c, const JoinSpec& j, uint64_t* d_off, uint64_t
 // lanes rather than one.
 constexpr int kDirT = 256;
 
+// Writes the outputs [o_begin, o_end) of probe row prow (build rows from
+// brow0) as one warp: unfiltered outputs go to pos0 + o, filtered ones are
+// packed with a ballot and one cursor claim per 32.
+template <bool FILTER>
+__device__ __forceinline__ void warp_emit(const JoinSpec& j, ColsOut out, uint64_t prow,
+                                          uint64_t brow0, uint64_t len, uint64_t pos0,
+                                          unsigned long long* cursor, uint64_t cap,
+                                          uint32_t* overflow) {
+  const uint32_t lane = lane_id();
+  const uint32_t lt = lanemask_lt();
+  for (uint64_t ob = 0; ob < len; ob += 32) {
+    const uint64_t o = ob + lane;
+    const bool valid = o < len;
+    uint32_t vals[kMaxK] = {0, 0, 0, 0};
+    bool keep = valid;
+    if (valid) {
+#pragma unroll
+      for (int k = 0; k < kMaxK; ++k)
+        if (k < (int)j.out_k) vals[k] = ref_value(j, j.out[k], prow, brow0 + o);
+      if (FILTER) {
+        for (uint32_t q = 0; q < j.n_eq; ++q)
+          keep &= ref_value(j, j.eq[q][0], prow, brow0 + o) == ref_value(j, j.eq[q][1], prow, brow0 + o);
+        for (uint32_t q = 0; q < j.n_neq; ++q)
+          keep &= ref_value(j, j.neq[q][0], prow, brow0 + o) != ref_value(j, j.neq[q][1], prow, brow0 + o);
+      }
+    }
+    uint64_t pos;
+    if (FILTER) {
+      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+      uint64_t cb = 0;
+      if (lane == 0 && bal) cb = atomicAdd(cursor, (unsigned long long)__popc(bal));
+      cb = __shfl_sync(0xffffffffu, cb, 0);
+      pos = cb + __popc(bal & lt);
+      if (bal && cb + __popc(bal) > cap && lane == 0) atomicOr(overflow, 1u);
+    } else {
+      pos = pos0 + o;
+    }
+    if (keep && pos < cap) {
+#pragma unroll
+      for (int k = 0; k < kMaxK; ++k)
+        if (k < (int)j.out_k) out.c[k][pos] = vals[k];
+    }
+  }
+}
+
 template <bool FILTER>
 __global__ void __launch_bounds__(kDirT) k_join_direct(const JoinSpec j, ColsOut out,
                                                        unsigned long long* cursor, uint64_t cap,
                                                        unsigned long long* total,
-                                                       uint32_t* overflow) {
+                                                       uint32_t* overflow, HeavyList heavy) {
   const uint32_t lane = lane_id();
   const uint32_t lt = lanemask_lt();
   const uint64_t mask = j.slots - 1;
@@ -243,6 +288,36 @@ __global__ void __launch_bounds__(kDirT) k_join_direct(const JoinSpec j, ColsOut
     const uint64_t row = w * 32 + lane;
     uint32_t st = 0, cnt = 0;
     if (row < j.n_probe) cnt = lookup(j, mask, row, &st);
+    // a long range becomes chunks of the heavy list
+    const bool hv = cnt > kHeavyChunk;
+    const uint32_t hmask = __ballot_sync(0xffffffffu, hv);
+    if (hmask) {
+      if (hv) {
+        atomicAdd(total, (unsigned long long)cnt);
+        uint64_t out0 = 0;
+        bool ok = true;
+        if (!FILTER) {
+          out0 = atomicAdd(cursor, (unsigned long long)cnt);
+          ok = out0 + cnt <= cap;
+        }
+        const uint32_t nch = (cnt + kHeavyChunk - 1) / kHeavyChunk;
+        const uint64_t at = ok ? atomicAdd((unsigned long long*)heavy.n, (unsigned long long)nch) : 0;
+        ok &= at + nch <= heavy.cap;
+        if (ok) {
+          for (uint32_t q = 0; q < nch; ++q) {
+            HeavyChunk h;
+            h.prow = row;
+            h.out0 = out0 + (uint64_t)q * kHeavyChunk;
+            h.brow = st + q * kHeavyChunk;
+            h.len = q + 1 < nch ? kHeavyChunk : cnt - q * kHeavyChunk;
+            heavy.e[at + q] = h;
+          }
+        } else {
+          atomicOr(overflow, 1u);
+        }
+      }
+      if (hv) cnt = 0;
+    }
     uint64_t inc = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -309,8 +384,24 @@ __global__ void __launch_bounds__(kDirT) k_join_direct(const JoinSpec j, ColsOut
   }
 }
 
+// The heavy list: one warp per chunk, grid-stride over the chunks the
+// direct kernel listed (their number is read from device memory).
+template <bool FILTER>
+__global__ void __launch_bounds__(kDirT) k_join_heavy(const JoinSpec j, ColsOut out,
+                                                      unsigned long long* cursor, uint64_t cap,
+                                                      uint32_t* overflow, HeavyList heavy) {
+  const uint64_t nwarps = ((uint64_t)gridDim.x * kDirT) >> 5;
+  uint64_t n = *heavy.n;
+  if (n > heavy.cap) n = heavy.cap;
+  for (uint64_t w = ((uint64_t)blockIdx.x * kDirT + threadIdx.x) >> 5; w < n; w += nwarps) {
+    const HeavyChunk h = heavy.e[w];
+    warp_emit<FILTER>(j, out, h.prow, h.brow, h.len, h.out0, cursor, cap, overflow);
+  }
+}
+
 cudaError_t join_direct(Ctx& c, const JoinSpec& j, ColsOut out, uint64_t* d_cursor,
-                        uint64_t out_cap, uint64_t* d_total, uint32_t* d_overflow) {
+                        uint64_t out_cap, uint64_t* d_total, uint32_t* d_overflow,
+                        const HeavyList& heavy) {
   if (j.n_probe == 0) return cudaSuccess;
   uint64_t blocks = (j.n_probe + kDirT - 1) / kDirT;
   if (blocks > 152 * 16) blocks = 152 * 16;
@@ -318,10 +409,15 @@ cudaError_t join_direct(Ctx& c, const JoinSpec& j, ColsOut out, uint64_t* d_curs
   ProfScope p(c, kJoinDirect, (4.0 + 16.0 + 4.0 * j.out_k) * j.n_probe);
   auto* cur = reinterpret_cast<unsigned long long*>(d_cursor);
   auto* tot = reinterpret_cast<unsigned long long*>(d_total);
-  if (filter)
-    k_join_direct<true><<<(unsigned)blocks, kDirT, 0, c.st>>>(j, out, cur, out_cap, tot, d_overflow);
-  else
-    k_join_direct<false><<<(unsigned)blocks, kDirT, 0, c.st>>>(j, out, cur, out_cap, tot, d_overflow);
+  if (filter) {
+    k_join_direct<true><<<(unsigned)blocks, kDirT, 0, c.st>>>(j, out, cur, out_cap, tot, d_overflow,
+                                                              heavy);
+    k_join_heavy<true><<<152 * 8, kDirT, 0, c.st>>>(j, out, cur, out_cap, d_overflow, heavy);
+  } else {
+    k_join_direct<false><<<(unsigned)blocks, kDirT, 0, c.st>>>(j, out, cur, out_cap, tot,
+                                                               d_overflow, heavy);
+    k_join_heavy<false><<<152 * 8, kDirT, 0, c.st>>>(j, out, cur, out_cap, d_overflow, heavy);
+  }
   return cudaGetLastError();
 }
 

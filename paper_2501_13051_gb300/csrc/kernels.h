@@ -180,8 +180,10 @@ struct SelectSpec {
   uint32_t n_neq;
   Ref neq[4][2];
 };
+// Rows past out_cap are dropped and flagged: kErrCapacity in the error word,
+// or *soft_overflow = 1 when soft_overflow is non-null.
 cudaError_t select_project(Ctx& c, const SelectSpec& s, ColsOut out, uint64_t* d_cursor,
-                           uint64_t out_cap);
+                           uint64_t out_cap, uint32_t* soft_overflow = nullptr);
 
 // last_round[v] = round for every instance id v < n_instances present in the
 // sorted instance column inst (n rows).
@@ -229,11 +231,30 @@ cudaError_t join_features(Ctx& c, const uint32_t* pk0, const uint32_t* pk1, uint
                           const uint32_t* bk0, const uint32_t* bk1, uint64_t nb,
                           const JoinFeatureHost& hf, float* f);
 
+// Work list of the single-pass join: a probe row whose range holds more
+// than kHeavyChunk outputs is cut into chunks of at most kHeavyChunk that
+// any warp of a second kernel takes, so one hot key does not serialise a
+// warp (the skew Section 4 answers with output partitioning).
+constexpr uint32_t kHeavyChunk = 2048;
+struct HeavyChunk {
+  uint64_t prow;  // probe row
+  uint64_t out0;  // first output position (unfiltered joins)
+  uint32_t brow;  // first build row of the chunk
+  uint32_t len;   // outputs in the chunk
+};
+struct HeavyList {
+  HeavyChunk* e = nullptr;
+  uint64_t* n = nullptr;  // device counter, zeroed by the caller
+  uint64_t cap = 0;
+};
+
 // Single-pass join write sized by a prediction: every probe row claims its
 // range at *d_cursor (atomic, one per warp); survivors are written when the
 // claim fits below out_cap, else *d_overflow is set and nothing more of that
-// warp is written.  *d_total receives the unfiltered join size.
+// warp is written.  *d_total receives the unfiltered join size.  Rows with
+// long ranges go through the heavy list (a full list also sets *d_overflow).
 cudaError_t join_direct(Ctx& c, const JoinSpec& j, ColsOut out, uint64_t* d_cursor,
-                        uint64_t out_cap, uint64_t* d_total, uint32_t* d_overflow);
+                        uint64_t out_cap, uint64_t* d_total, uint32_t* d_overflow,
+                        const HeavyList& heavy);
 
 }  // namespace cdl

@@ -175,13 +175,14 @@ cudaError_t mark_instances(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_
 }
 
 cudaError_t select_project(Ctx& c, const SelectSpec& s, ColsOut out, uint64_t* d_cursor,
-                           uint64_t out_cap) {
+                           uint64_t out_cap, uint32_t* soft_overflow) {
   if (s.n == 0) return cudaSuccess;
   const uint64_t blocks = (s.n + kST * kSItems - 1) / (kST * kSItems);
   ProfScope p(c, kSelect, 4.0 * s.in_k * s.n + 4.0 * s.out_k * s.n);
   k_select<<<(unsigned)blocks, kST, 0, c.st>>>(s, out,
                                                reinterpret_cast<unsigned long long*>(d_cursor),
-                                               out_cap, c.d_err);
+                                               out_cap,
+                                               soft_overflow ? soft_overflow : c.d_err);
   return cudaGetLastError();
 }
 

@@ -150,3 +150,42 @@ def test_estimator_without_weights_is_exact(cdl, oracle_lib):
         got = e.export("path")
     assert st.est_predictions == 0
     assert np.array_equal(got, oracle_lib.run_program(prog).relations["path"])
+
+
+def constant_network(log2_size):
+    """Parameters of a network that predicts log2_size for every join (all
+    weights zero, output bias set): a prediction large enough to hold the
+    join, so the single-pass path writes it."""
+    p = np.zeros(cdl_params(), dtype=np.float32)
+    p[-1] = log2_size
+    return p
+
+
+def cdl_params():
+    from paper_2501_13051_gb300 import cdl as C
+    return C.MLP_PARAMS
+
+
+def hot_key_program(with_filter):
+    # one key matches 10,000 build rows: every probe row on it is cut into
+    # chunks of the single-pass join's work list
+    hub = np.stack([np.full(10_000, 7), np.arange(10_000)], 1)
+    hub = np.concatenate([hub, [[1, 2], [1, 3], [2, 5]]])
+    src = np.stack([np.arange(30), np.where(np.arange(30) % 3 == 0, 1, 7)], 1)
+    neq = (("x", "y"),) if with_filter else ()
+    return W.Program(arity={"hub": 2, "src": 2, "out": 2},
+                     edb={"hub": hub.astype(np.uint32), "src": src.astype(np.uint32)},
+                     rules=[W.Rule(("out", ("x", "y")), (("src", ("x", "h")), ("hub", ("h", "y"))),
+                                   neq)])
+
+
+@pytest.mark.parametrize("with_filter", [False, True])
+def test_hot_keys_through_the_single_pass_join(cdl, oracle_lib, with_filter):
+    prog = hot_key_program(with_filter)
+    want = oracle_lib.run_program(prog)
+    with cdl.Engine(estimator=1, est_params=constant_network(20.0)) as e:
+        e.load_program(prog)
+        st = e.run()
+        got = e.export("out")
+    assert np.array_equal(got, want.relations["out"])
+    assert st.est_predictions > 0 and st.est_overflows == 0
