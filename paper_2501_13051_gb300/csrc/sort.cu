@@ -60,16 +60,21 @@ __global__ void __launch_bounds__(T) k_radix_upsweep(ColsIn in, uint64_t n, Pass
   for (int i = threadIdx.x; i < R; i += kRT) tile_hist[(uint64_t)i * ntiles + blockIdx.x] = h[i];
 }
 
+// Three resident blocks of 512 threads (or six of 256) per SM: registers
+// capped at 42, shared memory carved out to the maximum by the launcher.
 template <int K, int BITS, int T>
-__global__ void __launch_bounds__(T) k_radix_scatter(ColsIn in, ColsOut out, uint64_t n, PassP p,
-                                                     const uint64_t* __restrict__ off,
-                                                     uint64_t ntiles) {
+__global__ void __launch_bounds__(T, 1536 / T) k_radix_scatter(ColsIn in, ColsOut out, uint64_t n,
+                                                             PassP p,
+                                                             const uint64_t* __restrict__ off,
+                                                             uint64_t ntiles) {
   constexpr int R = 1 << BITS;
   constexpr int kRT = T, kRTile = T * kRItems, kRW = T / 32;
   constexpr int DPT = (R + kRT - 1) / kRT;
   __shared__ uint32_t wh[kRW][R];  // per-warp digit counts, then per-warp offsets
   __shared__ uint32_t tstart[R];   // tile-local start of each digit's run
-  __shared__ uint64_t gstart[R];   // global start of this tile's run of each digit
+  __shared__ uint64_t gstart[R];   // global start of this tile's run of each digit, less its
+                                   // tile-local start (an item at tile position i goes to
+                                   // gstart[d] + i)
   __shared__ uint32_t red[kRT / 32 + 1];
   extern __shared__ uint32_t stage[];  // K x kRTile
   for (int i = threadIdx.x; i < kRW * R; i += kRT) (&wh[0][0])[i] = 0;
@@ -143,6 +148,8 @@ __global__ void __launch_bounds__(T) k_radix_scatter(ColsIn in, ColsOut out, uin
       for (int k = 0; k < K; ++k) stage[k * kRTile + pos] = v[it][k];
     }
   }
+  // one tile (off null): its sorted order is the output order, g = i
+  for (int d = threadIdx.x; d < R; d += kRT) gstart[d] = off ? gstart[d] - tstart[d] : 0ull;
   __syncthreads();
   const uint32_t tile_n = (uint32_t)(n - base < (uint64_t)kRTile ? n - base : kRTile);
   for (uint32_t i = threadIdx.x; i < tile_n; i += kRT) {
@@ -150,7 +157,7 @@ __global__ void __launch_bounds__(T) k_radix_scatter(ColsIn in, ColsOut out, uin
 #pragma unroll
     for (int k = 0; k < K; ++k) t[k] = stage[k * kRTile + i];
     const uint32_t d = digit_of<K>(t, p);
-    const uint64_t g = off ? gstart[d] + (i - tstart[d]) : (uint64_t)i;
+    const uint64_t g = gstart[d] + i;
 #pragma unroll
     for (int k = 0; k < K; ++k) out.c[k][g] = t[k];
   }
@@ -182,6 +189,9 @@ cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uin
   const size_t smem = sizeof(uint32_t) * K * kRTile;
   cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<K, BITS, T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_radix_scatter<K, BITS, T>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   ColsOut src = a, dst = b;
   bool flip = false;
