@@ -13,7 +13,13 @@ relations' sizes summed over the steps / device time of the steps).
                   [--workload NAME] [--scale S]
 
 Workloads: sg-forest-200k (default), tc-er-1000-1500, points-to (scale S of
-2M variables / 4M assign / 1M dereference, Zipf 1.1), owl-rl-20m.
+2M variables / 4M assign / 1M dereference, Zipf 1.1; default 2^-9),
+owl-rl-20m, batched-512 (512 TC / SG instances in one batched run).  Each
+runs in the form it names: points-to and owl-rl-20m with the learned
+join-size estimator (trained first, untimed, on another seed), batched-512
+with the estimator and the autotuner (six tuning runs first, untimed).
+Those lines also carry the plain exact form timed the same way, and
+batched-512 the same instances run one after another.
 
 Under torchrun each rank runs an independent instance (seed + rank): the
 fixpoint has no exchange step here, so ranks are replicas and the value is
