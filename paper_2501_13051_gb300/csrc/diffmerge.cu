@@ -129,9 +129,41 @@ __device__ __forceinline__ uint64_t count_le_global(const ColsIn& F, uint64_t lo
   return lo;
 }
 
-// Persistent over tiles (grid = resident blocks): a tile without New tuples
-// costs one store, so a round whose few new tuples meet a large Full does
-// not pay one block launch per Full tile.
+// Co-rank and repeat test of New tuple j (row of U) against the Full slice
+// F[a0, a1), staged in shared memory (s) for dense tiles; returns the
+// co-rank or kRepeat.
+template <int K, bool DENSE>
+__device__ __forceinline__ uint32_t co_rank(const ColsIn& F, const ColsIn& U, const uint32_t* s,
+                                            uint64_t a0, uint64_t a1, uint64_t j) {
+  uint32_t v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = __ldg(U.c[k] + j);
+  if (j > 0 && eq_at<K>(U, j - 1, v)) return kRepeat;
+  // the Full tuple just before v in merged order is F[a0 + p - 1]
+  const uint32_t p = DENSE ? count_le_smem<K>(s, (uint32_t)(a1 - a0), v)
+                           : (uint32_t)(count_le_global<K>(F, a0, a1, v) - a0);
+  bool rep;
+  if (p > 0) {
+    if (DENSE) {
+      bool e = true;
+#pragma unroll
+      for (int k = 0; k < K; ++k) e &= s[k * kDTile + p - 1] == v[k];
+      rep = e;
+    } else {
+      rep = eq_at<K>(F, a0 + p - 1, v);
+    }
+  } else {
+    rep = a0 > 0 && eq_at<K>(F, a0 - 1, v);
+  }
+  return rep ? kRepeat : p;
+}
+
+// Persistent over groups of eight tiles (grid = resident blocks).  Each warp
+// takes one tile of the group: a tile without New tuples costs one store, a
+// sparse one (New < Full / 16) is searched by its warp alone with cached
+// global loads; dense tiles are then taken by the whole block, which stages
+// their Full slice in shared memory.  So a round whose few new tuples meet a
+// large Full keeps every warp busy instead of one block per tile.
 template <int K>
 __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t nF, uint64_t nU,
                                                    const uint64_t* __restrict__ splits,
@@ -140,18 +172,44 @@ __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t 
                                                    uint64_t ntiles) {
   extern __shared__ uint32_t s[];  // K x kDTile: the Full slice of a dense tile
   __shared__ uint32_t red[kDT / 32 + 1];
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const uint64_t d0 = tile * kDTile;
-    const uint64_t d1 = d0 + kDTile < nF + nU ? d0 + kDTile : nF + nU;
-    const uint64_t a0 = splits[tile], a1 = splits[tile + 1];
-    const uint64_t b0 = d0 - a0, b1 = d1 - a1;
-    const uint32_t na = (uint32_t)(a1 - a0), nb = (uint32_t)(b1 - b0);
-    if (nb == 0) {  // uniform over the block
-      if (threadIdx.x == 0) tile_cnt[tile] = 0;
-      continue;
+  constexpr int kW = kDT / 32;
+  __shared__ uint32_t dense[kW];
+  __shared__ uint32_t n_dense;
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  for (uint64_t g = blockIdx.x; g * kW < ntiles; g += gridDim.x) {
+    if (threadIdx.x == 0) n_dense = 0;
+    __syncthreads();
+    const uint64_t tile = g * kW + warp;
+    if (tile < ntiles) {
+      const uint64_t d0 = tile * kDTile;
+      const uint64_t d1 = d0 + kDTile < nF + nU ? d0 + kDTile : nF + nU;
+      const uint64_t a0 = splits[tile], a1 = splits[tile + 1];
+      const uint64_t b0 = d0 - a0, b1 = d1 - a1;
+      const uint64_t na = a1 - a0, nb = b1 - b0;
+      if (nb * 16 < na || nb == 0) {
+        uint32_t cnt = 0;
+        for (uint64_t j = b0 + lane; j < b1; j += 32) {
+          const uint32_t p = co_rank<K, false>(F, U, s, a0, a1, j);
+          corank[j] = p;
+          cnt += p == kRepeat ? 0u : 1u;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) tile_cnt[tile] = cnt;
+      } else if (lane == 0) {
+        dense[atomicAdd(&n_dense, 1u)] = warp;
+      }
     }
-    const bool dense = (uint64_t)nb * 16 >= na;
-    if (dense) {  // stage the Full slice, eight loads per column in flight
+    __syncthreads();
+    const uint32_t nd = n_dense;
+    for (uint32_t q = 0; q < nd; ++q) {
+      const uint64_t t = g * kW + dense[q];
+      const uint64_t d0 = t * kDTile;
+      const uint64_t d1 = d0 + kDTile < nF + nU ? d0 + kDTile : nF + nU;
+      const uint64_t a0 = splits[t], a1 = splits[t + 1];
+      const uint64_t b0 = d0 - a0, b1 = d1 - a1;
+      const uint32_t na = (uint32_t)(a1 - a0);
+      // stage the Full slice, eight loads per column in flight
       constexpr int kS = 8;
       for (uint32_t base = 0; base < na; base += kS * kDT) {
         uint32_t v[kS][K];
@@ -171,37 +229,17 @@ __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t 
         }
       }
       __syncthreads();
-    }
-    uint32_t cnt = 0;
-    for (uint64_t j = b0 + threadIdx.x; j < b1; j += kDT) {
-      uint32_t v[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) v[k] = __ldg(U.c[k] + j);
-      bool rep = j > 0 && eq_at<K>(U, j - 1, v);
-      uint32_t p = 0;
-      if (!rep) {
-        // the Full tuple just before v in merged order is F[a0 + p - 1]
-        p = dense ? count_le_smem<K>(s, na, v) : (uint32_t)(count_le_global<K>(F, a0, a1, v) - a0);
-        if (p > 0) {
-          if (dense) {
-            bool e = true;
-#pragma unroll
-            for (int k = 0; k < K; ++k) e &= s[k * kDTile + p - 1] == v[k];
-            rep = e;
-          } else {
-            rep = eq_at<K>(F, a0 + p - 1, v);
-          }
-        } else {
-          rep = a0 > 0 && eq_at<K>(F, a0 - 1, v);
-        }
+      uint32_t cnt = 0;
+      for (uint64_t j = b0 + threadIdx.x; j < b1; j += kDT) {
+        const uint32_t p = co_rank<K, true>(F, U, s, a0, a1, j);
+        corank[j] = p;
+        cnt += p == kRepeat ? 0u : 1u;
       }
-      corank[j] = rep ? kRepeat : p;
-      cnt += rep ? 0u : 1u;
+      uint32_t tot;
+      block_exclusive_sum<kDT, uint32_t>(cnt, red, &tot);
+      if (threadIdx.x == 0) tile_cnt[t] = tot;
+      __syncthreads();  // the next dense tile reuses s and red
     }
-    uint32_t tot;
-    block_exclusive_sum<kDT, uint32_t>(cnt, red, &tot);
-    if (threadIdx.x == 0) tile_cnt[tile] = tot;
-    __syncthreads();  // the next tile reuses s and red
   }
 }
 
@@ -334,7 +372,8 @@ cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, u
     if (e != cudaSuccess) return e;
     resident = (per_sm > 0 ? per_sm : 1) * sms;
   }
-  const uint64_t count_grid = tiles < (uint64_t)resident ? tiles : (uint64_t)resident;
+  const uint64_t groups = (tiles + kDT / 32 - 1) / (kDT / 32);  // eight tiles per group
+  const uint64_t count_grid = groups < (uint64_t)resident ? groups : (uint64_t)resident;
   {
     // New read, co-ranks written; Full sectors are read only where touched
     ProfScope p(c, kDiffCount, (4.0 * K + 4.0) * n_fresh);
