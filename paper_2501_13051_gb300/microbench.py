@@ -12,6 +12,11 @@ pairs with 18-bit columns), diff_merge (n sorted full pairs against n/8
 sorted new pairs, half of them already in full), scan (n counts).  Inputs
 exceed the 129 MB L2 for n >= 2^24, and each timed repeat is preceded by an
 L2-sized write.  Used for the ncu captures of single kernels.
+
+--dist zipf draws the keys Zipf(1.1) over the same domain (the join's probe
+keys against unique build keys, so the output stays n rows).  --sweep runs
+every step at 2^24, 2^26 and 2^28 (diff_merge and the Zipf cases up to
+2^26) for both distributions and prints one JSON line per case.
 """
 from __future__ import annotations
 
@@ -28,12 +33,86 @@ def _pairs(rng, n, bits=18):
     return (keys >> np.uint64(bits)).astype(np.uint32), (keys & np.uint64((1 << bits) - 1)).astype(np.uint32)
 
 
+def _zipf(rng, n, universe, s=1.1):
+    """Zipf(s) ranks over [0, universe) by inverse CDF, scattered by a
+    permutation so hot keys are not the small ones."""
+    w = np.arange(1, universe + 1, dtype=np.float64) ** -s
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    r = np.searchsorted(cdf, rng.random(n), side="right")
+    return rng.permutation(universe).astype(np.uint32)[np.minimum(r, universe - 1)]
+
+
+def _bits(v):
+    return int(v.max()).bit_length() if v.size else 0
+
+
+def make_case(step, n, dist, rng, dev, cdl):
+    """(run, algorithmic bytes) of one step on n synthetic tuples."""
+    keys = (lambda m, u: _zipf(rng, m, u)) if dist == "zipf" else \
+        (lambda m, u: rng.integers(0, u, size=m).astype(np.uint32))
+    if step == "diff_merge":
+        f0, f1 = _pairs(rng, n)
+        nu = max(1, n // 8)
+        pick = np.sort(rng.choice(n, size=nu // 2, replace=False))
+        u0 = np.concatenate([f0[pick], keys(nu - nu // 2, 1 << 18)])
+        u1 = np.concatenate([f1[pick], keys(nu - nu // 2, 1 << 18)])
+        o = np.lexsort((u1, u0))
+        F, U = [dev(f0), dev(f1)], [dev(u0[o]), dev(u1[o])]
+        run = lambda: cdl.diff_merge(F, U)
+        nd = len(run()[0][0])
+        return run, 8 * (n + nu) + 8 * (n + nd) + 8 * nd
+    if step == "sort":
+        c0, c1 = keys(n, 1 << 18), keys(n, 1 << 18)
+        C = [dev(c0), dev(c1)]
+        b0, b1 = _bits(c0), _bits(c1)
+        total = b0 + b1
+        npass = (total + 7) // 8
+        # upsweep: 4 B per column holding bits of the pass's digit; scatter:
+        # both columns read and written
+        up = sum(4 * ((lo < b1) + (lo + 8 > b1)) for lo in range(0, total, 8))
+        return (lambda: cdl.sort_unique(C)), (up + 16 * npass) * n
+    if step == "scan":
+        c = dev(rng.integers(0, 100, size=n).astype(np.uint32))
+        return (lambda: cdl.exclusive_scan(c)), 16 * n
+    if step == "hash":
+        k = dev(np.sort(keys(n, n // 2)))
+        return (lambda: cdl.hash_build(k)), 4 * n + 16 * (n // 2)
+    # join: build keys unique and sorted, probe keys over the same domain
+    b0 = np.sort(rng.permutation(2 * n)[:n].astype(np.uint32))
+    b1 = rng.integers(0, 1 << 30, size=n).astype(np.uint32)
+    p0 = b0[keys(n, n)]
+    p1 = rng.integers(0, 1 << 30, size=n).astype(np.uint32)
+    P, B = [dev(p0), dev(p1)], [dev(b0), dev(b1)]
+    run = lambda: cdl.join(P, 0, B, 0, [(0, 1), (1, 1)])
+    total = len(run()[0])
+    return run, (4 + 16 + 4 + 12) * n + 4 * n + 4 * n + (4 + 8) * total
+
+
+def time_case(run, repeat, flush):
+    import torch
+    run()  # warm-up
+    times = []
+    for _ in range(repeat):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        run()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    return float(np.median(times))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--step", required=True, choices=["hash", "join", "sort", "diff_merge", "scan"])
+    ap.add_argument("--step", choices=["hash", "join", "sort", "diff_merge", "scan"])
     ap.add_argument("--n", type=int, default=1 << 24)
     ap.add_argument("--repeat", type=int, default=5)
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--dist", default="uniform", choices=["uniform", "zipf"])
+    ap.add_argument("--sweep", action="store_true")
     args = ap.parse_args()
 
     import torch
@@ -43,57 +122,22 @@ def main():
     rng = np.random.default_rng(args.seed)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    n = args.n
-    if args.step == "diff_merge":
-        f0, f1 = _pairs(rng, n)
-        nu = max(1, n // 8)
-        pick = np.sort(rng.choice(n, size=nu // 2, replace=False))
-        u0 = np.concatenate([f0[pick], rng.integers(0, 1 << 18, size=nu - nu // 2).astype(np.uint32)])
-        u1 = np.concatenate([f1[pick], rng.integers(0, 1 << 18, size=nu - nu // 2).astype(np.uint32)])
-        o = np.lexsort((u1, u0))
-        F, U = [dev(f0), dev(f1)], [dev(u0[o]), dev(u1[o])]
-        run = lambda: cdl.diff_merge(F, U)
-        nd = len(run()[0][0])
-        algo = 8 * (n + nu) + 8 * (n + nd) + 8 * nd
-    elif args.step == "sort":
-        c0 = rng.integers(0, 1 << 18, size=n).astype(np.uint32)
-        c1 = rng.integers(0, 1 << 18, size=n).astype(np.uint32)
-        C = [dev(c0), dev(c1)]
-        run = lambda: cdl.sort_unique(C)
-        algo = None  # reported per kernel class by the engine profiler instead
-    elif args.step == "scan":
-        c = dev(rng.integers(0, 100, size=n).astype(np.uint32))
-        run = lambda: cdl.exclusive_scan(c)
-        algo = 4 * n + 4 * n + 8 * n
-    elif args.step == "hash":
-        k = dev(np.sort(rng.integers(0, n // 2, size=n).astype(np.uint32)))
-        run = lambda: cdl.hash_build(k)
-        algo = 4 * n + 16 * (n // 2)
+    if args.sweep:
+        cases = [(st, 1 << e, d) for st in ("hash", "join", "sort", "scan", "diff_merge")
+                 for e in (24, 26, 28) for d in ("uniform", "zipf")
+                 if not ((st == "diff_merge" or d == "zipf") and e > 26)
+                 and not (st == "scan" and d == "zipf")]
     else:
-        b0 = np.sort(rng.integers(0, n, size=n).astype(np.uint32))
-        b1 = rng.integers(0, 1 << 30, size=n).astype(np.uint32)
-        p0 = rng.integers(0, n, size=n).astype(np.uint32)
-        p1 = rng.integers(0, 1 << 30, size=n).astype(np.uint32)
-        P, B = [dev(p0), dev(p1)], [dev(b0), dev(b1)]
-        run = lambda: cdl.join(P, 0, B, 0, [(0, 1), (1, 1)])
-        total = len(run()[0])
-        algo = (4 + 16 + 4 + 12) * n + 4 * n + 4 * n + (4 + 8) * total
-    run()  # warm-up
-    times = []
-    for _ in range(args.repeat):
-        flush.fill_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record()
-        run()
-        b.record()
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b))
-    ms = float(np.median(times))
-    out = {"step": args.step, "n": n, "ms": ms}
-    if algo:
-        out["algo_GBps"] = algo / (ms * 1e-3) / 1e9
-    print(json.dumps(out), flush=True)
+        if not args.step:
+            ap.error("--step or --sweep")
+        cases = [(args.step, args.n, args.dist)]
+    for step, n, dist in cases:
+        run, algo = make_case(step, n, dist, rng, dev, cdl)
+        ms = time_case(run, args.repeat, flush)
+        print(json.dumps({"step": step, "n": n, "dist": dist, "ms": ms,
+                          "algo_GBps": algo / (ms * 1e-3) / 1e9}), flush=True)
+        del run
+        torch.cuda.empty_cache()
 
 
 if __name__ == "__main__":
