@@ -18,8 +18,9 @@ owl-rl-20m, batched-512 (512 TC / SG instances in one batched run).  Each
 runs in the form it names: points-to and owl-rl-20m with the learned
 join-size estimator (trained first, untimed, on another seed), batched-512
 with the estimator and the autotuner (six tuning runs first, untimed).
-Those lines also carry the plain exact form timed the same way, and
-batched-512 the same instances run one after another.
+tc-er-1000-1500 runs its rounds after the first semi-naive one as one CUDA
+graph (a device-side loop).  Those lines also carry the plain form timed
+the same way, and batched-512 the same instances run one after another.
 
 Under torchrun each rank runs an independent instance (seed + rank): the
 fixpoint has no exchange step here, so ranks are replicas and the value is
@@ -57,9 +58,10 @@ WORKLOADS = {
                            desc="same-generation on a random forest, 200000 nodes, "
                                 "p_parent 0.98, +2% cross edges",
                            sample=dict(kind="sg", n=10_000, seed=2)),
-    "tc-er-1000-1500": dict(kind="tc", n=1000, m=1500, seed=1,
+    "tc-er-1000-1500": dict(kind="tc", n=1000, m=1500, seed=1, graph=True,
                             desc="transitive closure on a directed Erdos-Renyi graph, "
-                                 "1000 nodes, 1500 edges",
+                                 "1000 nodes, 1500 edges; rounds after the first semi-naive "
+                                 "one captured as one CUDA graph with a device-side loop",
                             sample=dict(kind="tc", n=1000, m=1500, seed=1)),
     "points-to": dict(kind="pt", scale=1 / 512, seed=3, learned=True,
                       desc="points-to analysis (valueFlow / memoryAlias / valueAlias), "
@@ -203,6 +205,15 @@ class ClockSampler:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi's start-up takes driver locks: let it reach its polling
+        # loop (first sample written) before the timed steps begin
+        t0 = time.time()
+        while time.time() - t0 < 5 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
+        time.sleep(0.25)
 
     def stop(self):
         if self.proc is None:
@@ -307,6 +318,8 @@ def bench_gb300(args, rank, world, dist):
                 rules(e)
                 e.run()
         form.update(autotune=1, tune_cache=cache)
+    if spec.get("graph"):
+        form.update(graph=True)
     trained = None
     if spec.get("learned"):
         params, nsamp, tsec = train_estimator(spec, rank)
@@ -457,6 +470,8 @@ def bench_gb300(args, rank, world, dist):
                                "fallbacks": int(st.est_overflows)}
     if spec.get("tune"):
         config["autotune"] = "6 tuning runs (untimed), then the cached choices"
+    if spec.get("graph"):
+        config["graph"] = "rounds 3.. as one CUDA graph (conditional while node)"
     if plain is not None:
         config["plain_exact"] = plain
         config["form_over_plain_exact"] = value / plain["tuples_per_s"]

@@ -106,6 +106,13 @@ typedef struct {
                            the results back to tune_cache at the end of cdl_run.  Results
                            never depend on it */
   const char* tune_cache; /* tuner file path (copied at cdl_create), or NULL: in memory */
+  int32_t graph;        /* 1: after the first semi-naive round, run the rounds of a program
+                           whose rules each join one derived atom with input relations as
+                           one CUDA graph: the round captured once, repeated by a device-side
+                           loop until the fixpoint (a round that outgrows the graph's buffers
+                           runs on the host, then the graph is rebuilt larger); other
+                           programs run as with 0.  Values >= 2: the same, with buffers
+                           starting at that many rows instead of 65,536 */
 } cdl_options;
 
 /* Fills *opts with the defaults (everything zero / NULL except the
@@ -170,6 +177,9 @@ typedef struct {
   uint64_t delta_cap;        /* its length */
   uint64_t* iters_per_instance; /* caller array of n_instances or NULL: for a batched run,
                                    the last round in which each instance derived a tuple */
+  uint64_t graph_rounds;  /* options.graph: rounds run by the captured graph's device loop */
+  uint64_t graph_builds;  /* options.graph: graphs captured (one more after each round that
+                             outgrew the graph's buffers) */
 } cdl_stats;
 
 /* Runs the semi-naive loop to the fixpoint on the engine's stream and waits

@@ -43,7 +43,8 @@ class Options(ctypes.Structure):
                 ("hash_load", ctypes.c_double), ("radix_bits", ctypes.c_uint32),
                 ("log_path", ctypes.c_char_p), ("est_margin", ctypes.c_double),
                 ("n_instances", ctypes.c_uint32), ("retire", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("tune_cache", ctypes.c_char_p)]
+                ("autotune", ctypes.c_int32), ("tune_cache", ctypes.c_char_p),
+                ("graph", ctypes.c_int32)]
 
 MLP_IN = 16
 MLP_PARAMS = 5313
@@ -71,7 +72,8 @@ class Stats(ctypes.Structure):
                 ("est_overflows", ctypes.c_uint64),
                 ("delta_per_round", ctypes.POINTER(ctypes.c_uint64)),
                 ("delta_cap", ctypes.c_uint64),
-                ("iters_per_instance", ctypes.POINTER(ctypes.c_uint64))]
+                ("iters_per_instance", ctypes.POINTER(ctypes.c_uint64)),
+                ("graph_rounds", ctypes.c_uint64), ("graph_builds", ctypes.c_uint64)]
 
 
 class ColRef(ctypes.Structure):
@@ -194,6 +196,8 @@ class RunStats:
     est_predictions: int = 0
     est_overflows: int = 0
     iters_per_instance: list = field(default_factory=list)
+    graph_rounds: int = 0
+    graph_builds: int = 0
 
 
 # kernel classes in cdl_kernel_profile order
@@ -223,7 +227,7 @@ class Engine:
     def __init__(self, *, device=None, stream=None, mem_limit=0, max_iters=0, spin_limit=0,
                  timing=False, hash_load=0.5, radix_bits=8, torch_alloc=True, estimator=0,
                  est_margin=1.0, est_params=None, n_instances=0, retire=True, autotune=0,
-                 tune_cache=None):
+                 tune_cache=None, graph=False):
         torch = _torch()
         L = lib()
         self._L = L
@@ -247,6 +251,7 @@ class Engine:
         opts.n_instances = n_instances
         opts.retire = 0 if retire else -1
         opts.autotune = autotune
+        opts.graph = int(graph)  # True / False, or a starting capacity in rows
         opts.tune_cache = os.fsencode(tune_cache) if tune_cache else None
         self.n_instances = n_instances
         self._opts = opts
@@ -360,7 +365,8 @@ class Engine:
         return RunStats(st.iterations, st.rounds, st.derived_tuples, st.seconds, st.algo_bytes,
                         st.joins, st.kernel_launches, [int(buf[i]) for i in range(min(st.rounds, cap))],
                         st.est_predictions, st.est_overflows,
-                        [int(inst[i]) for i in range(self.n_instances)])
+                        [int(inst[i]) for i in range(self.n_instances)],
+                        st.graph_rounds, st.graph_builds)
 
     # ---------------------------------------------------------- estimator
     def estimator_log(self):

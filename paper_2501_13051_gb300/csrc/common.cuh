@@ -190,4 +190,14 @@ __device__ __forceinline__ uint64_t warp_look_back(uint64_t* status, uint64_t ti
   return prefix;
 }
 
+// Device-sized launches (a round captured in a CUDA graph): the grid is
+// sized for a capacity known to the host, the actual size is read from
+// device memory and clamped to that capacity, so no access can leave the
+// buffers the capacity describes.  dn == nullptr: the size is `cap` itself.
+__device__ __forceinline__ uint64_t dev_size(const uint64_t* dn, uint64_t cap) {
+  if (!dn) return cap;
+  const uint64_t v = *dn;
+  return v < cap ? v : cap;
+}
+
 }  // namespace cdl

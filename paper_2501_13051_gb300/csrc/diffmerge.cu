@@ -65,10 +65,26 @@ __device__ __forceinline__ uint64_t merge_split(const ColsIn& F, uint64_t nF, co
   return lo;
 }
 
+// Inside a captured round, Full and the sizes come from device memory;
+// false when the merged relation would not fit its buffer.
+__device__ __forceinline__ bool resolve(const DevMerge& dm, ColsIn& F, uint64_t& nF, uint64_t& nU,
+                                        uint64_t& ntiles) {
+  if (!dm.n_full) return true;
+  F = *dm.full;
+  nF = dev_size(dm.n_full, nF);
+  nU = dev_size(dm.n_fresh, nU);
+  ntiles = (nF + nU + kDTile - 1) / kDTile;
+  return nF + nU <= dm.cap_merged;
+}
+
 template <int K>
 __global__ void k_merge_splits(ColsIn F, uint64_t nF, ColsIn U, uint64_t nU,
-                               uint64_t* __restrict__ splits, uint64_t ntiles) {
+                               uint64_t* __restrict__ splits, uint64_t ntiles, DevMerge dm) {
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!resolve(dm, F, nF, nU, ntiles)) {
+    if (t == 0) atomicOr(dm.overflow, 1u);
+    return;
+  }
   if (t > ntiles) return;
   const uint64_t d = t * kDTile < nF + nU ? t * kDTile : nF + nU;
   splits[t] = merge_split<K>(F, nF, U, nU, d);
@@ -169,8 +185,9 @@ __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t 
                                                    const uint64_t* __restrict__ splits,
                                                    uint32_t* __restrict__ corank,
                                                    uint32_t* __restrict__ tile_cnt,
-                                                   uint64_t ntiles) {
+                                                   uint64_t ntiles, DevMerge dm) {
   extern __shared__ uint32_t s[];  // K x kDTile: the Full slice of a dense tile
+  if (!resolve(dm, F, nF, nU, ntiles)) return;
   __shared__ uint32_t red[kDT / 32 + 1];
   constexpr int kW = kDT / 32;
   __shared__ uint32_t dense[kW];
@@ -253,10 +270,17 @@ __global__ void __launch_bounds__(kDT) k_merge_write(ColsIn F, uint64_t nF, Cols
                                                      const uint64_t* __restrict__ splits,
                                                      const uint32_t* __restrict__ corank,
                                                      const uint64_t* __restrict__ tile_pre,
-                                                     ColsOut D, ColsOut M) {
+                                                     ColsOut D, ColsOut M, DevMerge dm) {
   __shared__ uint32_t shift[kShiftWords];
   __shared__ uint32_t red[kDT / 32 + 1];
   const uint64_t tile = blockIdx.x;
+  uint64_t ntiles = 0;
+  if (!resolve(dm, F, nF, nU, ntiles)) return;
+  if (dm.n_full) {
+    if (tile >= ntiles) return;
+    D = *dm.delta;
+    M = *dm.merged;
+  }
   const uint64_t d0 = tile * kDTile;
   const uint64_t d1 = d0 + kDTile < nF + nU ? d0 + kDTile : nF + nU;
   const uint64_t a0 = splits[tile], a1 = splits[tile + 1];
@@ -342,11 +366,20 @@ uint64_t dm_tiles(uint64_t n_full, uint64_t n_fresh) {
   return (n_full + n_fresh + kDTile - 1) / kDTile;
 }
 
+// Tiles of a device-sized pair (0 when it does not fit): the scan's length.
+__global__ void k_dm_tiles(DevMerge dm, uint64_t nF, uint64_t nU, uint64_t* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ColsIn F{};
+  uint64_t ntiles = 0;
+  out[0] = resolve(dm, F, nF, nU, ntiles) ? ntiles : 0;
+}
+
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
 template <int K>
 cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, uint64_t n_fresh,
-                           ColsOut delta, ColsOut merged, uint64_t* d_ndelta, void* ws) {
+                           ColsOut delta, ColsOut merged, uint64_t* d_ndelta, void* ws,
+                           const DevMerge& dm) {
   const uint64_t tiles = dm_tiles(n_full, n_fresh);
   char* w = static_cast<char*>(ws);
   uint64_t* splits = reinterpret_cast<uint64_t*>(w);
@@ -358,6 +391,11 @@ cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, u
   uint32_t* corank = reinterpret_cast<uint32_t*>(w);
   w += up256((n_fresh ? n_fresh : 1) * 4);
   void* scan_ws = w;
+  uint64_t* d_tiles = nullptr;  // device-sized: the scan's length, after its workspace
+  if (dm.n_full) {
+    d_tiles = reinterpret_cast<uint64_t*>(w + scan_workspace(tiles));
+    k_dm_tiles<<<1, 32, 0, c.st>>>(dm, n_full, n_fresh, d_tiles);
+  }
   const size_t smem_count = sizeof(uint32_t) * K * kDTile;
   static int resident = 0;  // blocks of k_count_new<K> the whole GPU holds at once
   cudaError_t e = cudaSuccess;
@@ -377,19 +415,19 @@ cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, u
   {
     // New read, co-ranks written; Full sectors are read only where touched
     ProfScope p(c, kDiffCount, (4.0 * K + 4.0) * n_fresh);
-    k_merge_splits<K><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, c.st>>>(full, n_full, fresh,
-                                                                             n_fresh, splits, tiles);
+    k_merge_splits<K><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, c.st>>>(
+        full, n_full, fresh, n_fresh, splits, tiles, dm);
     k_count_new<K><<<(unsigned)count_grid, kDT, smem_count, c.st>>>(full, fresh, n_full, n_fresh,
-                                                                     splits, corank, cnt, tiles);
+                                                                     splits, corank, cnt, tiles, dm);
   }
-  e = exclusive_scan(c, cnt, tiles, pre, d_ndelta, scan_ws);
+  e = exclusive_scan(c, cnt, tiles, pre, d_ndelta, scan_ws, d_tiles);
   if (e != cudaSuccess) return e;
   // read Full, New and the co-ranks, write Full again; the delta part of the
   // writes (merged and delta) is added once its size is known
   const double mb = merged.c[0] ? 4.0 * K * n_full : 0.0;
   ProfScope p(c, kDiffMerge, 4.0 * K * (n_full + n_fresh) + 4.0 * n_fresh + mb);
   k_merge_write<K><<<(unsigned)tiles, kDT, 0, c.st>>>(full, n_full, fresh, n_fresh, splits, corank,
-                                                      pre, delta, merged);
+                                                      pre, delta, merged, dm);
   return cudaGetLastError();
 }
 
@@ -398,18 +436,20 @@ cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, u
 size_t diff_merge_workspace(uint64_t n_full, uint64_t n_fresh) {
   const uint64_t tiles = dm_tiles(n_full, n_fresh);
   return up256((tiles + 1) * 8) + up256(tiles * 4) + up256(tiles * 8) +
-         up256((n_fresh ? n_fresh : 1) * 4) + scan_workspace(tiles);
+         up256((n_fresh ? n_fresh : 1) * 4) + scan_workspace(tiles) + 256;
 }
 
 cudaError_t diff_merge(Ctx& c, uint32_t k, ColsIn full, uint64_t n_full, ColsIn fresh,
                        uint64_t n_fresh, ColsOut delta, ColsOut merged, uint64_t* d_ndelta,
-                       void* ws) {
+                       void* ws, const DevMerge* dm) {
   if (n_full + n_fresh == 0) return cudaMemsetAsync(d_ndelta, 0, sizeof(uint64_t), c.st);
+  const DevMerge none{};
+  const DevMerge& d = dm ? *dm : none;
   switch (k) {
-    case 1: return run_diff_merge<1>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws);
-    case 2: return run_diff_merge<2>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws);
-    case 3: return run_diff_merge<3>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws);
-    case 4: return run_diff_merge<4>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws);
+    case 1: return run_diff_merge<1>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws, d);
+    case 2: return run_diff_merge<2>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws, d);
+    case 3: return run_diff_merge<3>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws, d);
+    case 4: return run_diff_merge<4>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws, d);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -361,6 +361,43 @@ struct cdl_engine {
   DBuf heavy_buf;  // the single-pass join's list of long-range chunks
   HeavyList heavy;
   bool force_exact = false;  // rules are being redone without predictions
+  // rounds captured as a CUDA graph (option graph): the join steps of the
+  // first semi-naive round, recorded as they run, are the plan of every
+  // later round
+  struct GStep {
+    size_t rule = 0;
+    size_t t = 0;          // position in the rule's join chain (1-based)
+    JoinSpec js{};         // as planned; probe columns and size come from the device
+    bool last = false, filter = false;
+    uint32_t head = 0;     // relation the last step appends to
+    int probe_rel = -1;    // first step: the relation whose delta it probes
+    uint64_t seen_probe = 0, seen_total = 0;
+  };
+  std::vector<GStep> grec;
+  bool recording = false, grec_bad = false, graph_ready = false;
+  struct GRelRes {
+    uint32_t rel = 0;
+    DCols F[2], D[2], fresh, alt;
+    DBuf sort_ws, merge_ws;
+    RadixPlan plan;
+    bool sorted_in_alt = false;
+    uint64_t Fcap = 0, Ucap = 0;
+  };
+  struct GStepRes {
+    DBuf off, cws, wws;
+    size_t wbytes = 0;
+    DCols inter;
+    uint64_t pcap = 0, ocap = 0;
+  };
+  std::vector<GRelRes> grel;
+  std::vector<GStepRes> gstep;
+  std::vector<uint64_t> gcap_u, gcap_i, gcap_f;  // capacities by relation / step
+  DBuf gdev;
+  cudaGraph_t ggraph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  uint64_t glaunches_per_round = 0;
+  uint64_t g_rounds = 0, g_builds = 0;
+  static constexpr uint64_t kGraphRounds = 1 << 16;  // per-round sizes the device records
   DBuf inst_last;  // batched runs: last round each instance derived a tuple
   std::vector<uint64_t> h_inst;
   std::vector<uint8_t> inst_live, inst_conv;  // rows still in full; fixpoint reached
@@ -734,6 +771,7 @@ struct cdl_engine {
 
   // --------------------------------------------------------------- rules
   cdl_status eval_copy(const RuleR& rule, int ver) {
+    if (recording) grec_bad = true;
     const AtomR& a = rule.body[0];
     Src base = rel_src(a.rel, ver);
     if (base.n == 0) return CDL_OK;
@@ -776,6 +814,7 @@ struct cdl_engine {
   // Writes the head tuples of a rule whose join chain is a single table
   // (s) or empty (s == null: a body of variable-free atoms, all matched).
   cdl_status emit_from(const RuleR& rule, const Src* s, const Src& any) {
+    if (recording) grec_bad = true;
     SelectSpec sp{};
     if (s) {
       sp.in = s->in();
@@ -1083,6 +1122,23 @@ struct cdl_engine {
       const uint64_t total = h_ctl[kSlotScratch];
       ++joins;
       log_sample(total);
+      if (recording) {  // a step of a capturable plan: hash join, static build side
+        GStep g;
+        g.rule = (size_t)(&rule - rules.data());
+        g.t = t;
+        g.js = js;
+        g.last = last;
+        g.filter = filter;
+        g.head = rule.head.rel;
+        g.probe_rel = t == 1 ? P.rel : -1;
+        g.seen_probe = P.n;
+        g.seen_total = total;
+        const bool first_ok = t > 1 || (P.rel >= 0 && P.ver == kDelta && rels[P.rel]->idb);
+        const bool later_ok = t == 1 || P.rel < 0;
+        if (!ix || &P != &left || B.rel < 0 || rels[B.rel]->idb || !first_ok || !later_ok)
+          grec_bad = true;
+        grec.push_back(g);
+      }
       if (total == 0) return CDL_OK;
       ws.reset();
       const size_t wws = join_write_workspace(P.n, total);
@@ -1424,6 +1480,323 @@ struct cdl_engine {
     return CDL_OK;
   }
 
+  // ------------------------------------------------- rounds as a CUDA graph
+  // The plan recorded in the first semi-naive round can be captured when
+  // every rule with a derived relation in its body has exactly one such
+  // atom, every other atom is an input relation joined through its hash
+  // index, and every derived relation is the head of a recorded chain.
+  bool graph_plan() {
+    if (grec_bad || grec.empty() || opt.estimator) return false;
+    std::vector<bool> active(rels.size(), false);
+    for (size_t ri = 0; ri < rules.size(); ++ri) {
+      const RuleR& rule = rules[ri];
+      size_t idb_atoms = 0, var_atoms = 0;
+      for (const AtomR& a : rule.body) {
+        idb_atoms += rels[a.rel]->idb;
+        bool vars = false;
+        for (const Term& t : a.t) vars |= !t.is_const;
+        var_atoms += vars;
+      }
+      if (idb_atoms == 0) continue;  // fires in round 1 only
+      if (idb_atoms > 1 || rule.body.size() < 2) return false;
+      std::vector<const GStep*> chain;
+      for (const GStep& g : grec)
+        if (g.rule == ri) chain.push_back(&g);
+      if (chain.size() + 1 != var_atoms) return false;
+      for (size_t i = 0; i < chain.size(); ++i)
+        if (chain[i]->t != i + 1 || chain[i]->last != (i + 1 == chain.size())) return false;
+      active[rule.head.rel] = true;
+    }
+    for (size_t i = 0; i < rels.size(); ++i)
+      if (rels[i]->idb && !active[i]) return false;
+    return true;
+  }
+
+  void graph_release() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (ggraph) cudaGraphDestroy(ggraph);
+    gexec = nullptr;
+    ggraph = nullptr;
+    grel.clear();
+    gstep.clear();
+    gdev.reset();
+  }
+
+  // Device state layout inside gdev.
+  size_t g_off_next() const { return sizeof(GraphRel) * grel.size(); }
+  size_t g_off_ctl() const { return 2 * g_off_next(); }
+  size_t g_off_cursor() const { return g_off_ctl() + 64; }
+  size_t g_off_step() const { return g_off_cursor() + 8 * grel.size(); }
+  size_t g_off_round() const { return g_off_step() + 24 * gstep.size(); }
+  size_t g_bytes() const { return g_off_round() + 8 * kGraphRounds; }
+  char* gbase() const { return static_cast<char*>(gdev.p); }
+  GraphRel* g_cur() const { return reinterpret_cast<GraphRel*>(gbase()); }
+  GraphRel* g_next() const { return reinterpret_cast<GraphRel*>(gbase() + g_off_next()); }
+  GraphCtl* g_ctl() const { return reinterpret_cast<GraphCtl*>(gbase() + g_off_ctl()); }
+  uint64_t* g_cursor(size_t r) const { return reinterpret_cast<uint64_t*>(gbase() + g_off_cursor()) + r; }
+  uint64_t* g_step(size_t s, int w) const {  // 0 total, 1 base, 2 intermediate rows
+    return reinterpret_cast<uint64_t*>(gbase() + g_off_step()) + 3 * s + w;
+  }
+  uint64_t* g_round() const { return reinterpret_cast<uint64_t*>(gbase() + g_off_round()); }
+
+  // Buffers at the capacities in gcap_*, the relations' current versions
+  // copied in, and the round captured into the body of a device-side loop.
+  cdl_status graph_build(uint64_t rounds_done, uint64_t iterations) {
+    graph_release();
+    std::vector<int> slot(rels.size(), -1);
+    for (size_t i = 0; i < rels.size(); ++i)
+      if (rels[i]->idb) {
+        slot[i] = (int)grel.size();
+        grel.emplace_back();
+        grel.back().rel = (uint32_t)i;
+      }
+    gstep.resize(grec.size());
+    gdev = alloc(g_bytes());
+    if (!gdev.p) return fail(CDL_E_NOMEM, "graph state");
+    std::vector<GraphRel> cur(grel.size()), next(grel.size());
+    for (size_t j = 0; j < grel.size(); ++j) {
+      GRelRes& G = grel[j];
+      Relation& R = *rels[G.rel];
+      G.Ucap = gcap_u[G.rel];
+      G.Fcap = gcap_f[G.rel];
+      uint32_t bits[kMaxK];
+      for (uint32_t k = 0; k < R.arity; ++k) bits[k] = bits_of(R.bound[k]);
+      G.plan = make_radix_plan(R.arity, bits, radix_bits, 512);
+      G.sorted_in_alt = G.plan.npass % 2 == 1;
+      bool ok = true;
+      for (int side = 0; side < 2; ++side) {
+        ok &= alloc_cols(G.F[side], R.arity, G.Fcap);
+        ok &= alloc_cols(G.D[side], R.arity, G.Ucap);
+      }
+      ok &= alloc_cols(G.fresh, R.arity, G.Ucap) && alloc_cols(G.alt, R.arity, G.Ucap);
+      G.sort_ws = alloc(radix_workspace(G.Ucap, G.plan.bits, G.plan.threads));
+      G.merge_ws = alloc(diff_merge_workspace(G.Fcap, G.Ucap));
+      if (!ok || !G.sort_ws.p || !G.merge_ws.p) return fail(CDL_E_NOMEM, "graph buffers");
+      if (R.full.n > G.Fcap || R.delta.n > G.Ucap) return fail(CDL_E_CAPACITY, "graph capacities");
+      for (uint32_t k = 0; k < R.arity; ++k) {
+        cudaError_t e = cudaSuccess;
+        if (R.full.n)
+          e = cudaMemcpyAsync(G.F[0].c[k], R.full.c[k], 4 * R.full.n, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && R.delta.n)
+          e = cudaMemcpyAsync(G.D[0].c[k], R.delta.c[k], 4 * R.delta.n, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "graph state copy");
+      }
+      cur[j] = GraphRel{G.F[0].in(), G.D[0].in(), R.full.n, R.delta.n};
+      next[j] = GraphRel{G.F[1].in(), G.D[1].in(), 0, 0};
+    }
+    for (size_t s = 0; s < grec.size(); ++s) {
+      const GStep& g = grec[s];
+      GStepRes& S = gstep[s];
+      S.pcap = g.t == 1 ? gcap_u[g.probe_rel] : gstep[s - 1].ocap;
+      S.ocap = g.last ? gcap_u[g.head] : gcap_i[s];
+      S.off = alloc(8 * S.pcap);
+      S.cws = alloc(join_count_workspace(S.pcap));
+      S.wbytes = join_write_workspace(S.pcap, S.ocap);
+      S.wws = alloc(S.wbytes);
+      if (!S.off.p || !S.cws.p || !S.wws.p) return fail(CDL_E_NOMEM, "graph join buffers");
+      if (!g.last && !alloc_cols(S.inter, g.js.out_k, S.ocap)) return fail(CDL_E_NOMEM, "graph join buffers");
+    }
+    GraphCtl ctl{};
+    ctl.round = rounds_done;
+    ctl.iterations = iterations;
+    ctl.max_iters = opt.max_iters;
+    cudaError_t e = cudaMemsetAsync(gdev.p, 0, g_bytes(), st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g_cur(), cur.data(), sizeof(GraphRel) * cur.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g_next(), next.data(), sizeof(GraphRel) * next.size(),
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g_ctl(), &ctl, sizeof ctl, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "graph state");
+
+    // capture: one round inside a while node whose condition round_end sets
+    e = cudaGraphCreate(&ggraph, 0);
+    cudaGraphConditionalHandle loop{};
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&loop, ggraph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = loop;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, ggraph, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) return cuda_fail(e, "graph loop node");
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    // capture on a stream of its own (the engine's may be the legacy default
+    // stream, which cannot capture); the graph is launched on the engine's
+    cudaStream_t gst = nullptr;
+    e = cudaStreamCreateWithFlags(&gst, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "graph stream");
+    Profiler* saved = ctx.prof;
+    const cudaStream_t main_st = st;
+    Profiler counter;  // counts the captured launches, records no events
+    ctx.prof = &counter;
+    ctx.st = st = gst;
+    e = cudaStreamBeginCaptureToGraph(gst, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) e = graph_round(slot, loop);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(gst, &captured);
+    ctx.prof = saved;
+    ctx.st = st = main_st;
+    cudaStreamDestroy(gst);
+    glaunches_per_round = counter.total_launches;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, ggraph, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(e, "graph capture");
+    }
+    return CDL_OK;
+  }
+
+  // The launches of one round, each reading its sizes (and the current
+  // full / delta columns) from the device state.
+  cudaError_t graph_round(const std::vector<int>& slot, cudaGraphConditionalHandle loop) {
+    uint32_t* ovf = &g_ctl()->overflow;
+    cudaError_t e = cudaMemsetAsync(g_cursor(0), 0, 8 * grel.size(), st);
+    for (size_t s = 0; s < gstep.size() && e == cudaSuccess; ++s)
+      e = cudaMemsetAsync(g_step(s, 2), 0, 8, st);
+    for (size_t s = 0; s < grec.size() && e == cudaSuccess; ++s) {
+      const GStep& g = grec[s];
+      GStepRes& S = gstep[s];
+      JoinSpec js = g.js;
+      js.n_probe = S.pcap;
+      if (g.t == 1) {
+        GraphRel* c = g_cur() + slot[g.probe_rel];
+        js.dprobe = &c->D;
+        js.dn = &c->nD;
+      } else {
+        js.probe = gstep[s - 1].inter.in();
+        js.dprobe = nullptr;
+        js.dn = g_step(s - 1, 2);
+      }
+      GRelRes* H = g.last ? &grel[slot[g.head]] : nullptr;
+      uint64_t* cursor = g.last ? g_cursor(slot[g.head]) : g_step(s, 2);
+      const ColsOut out = g.last ? H->fresh.out() : S.inter.out();
+      e = join_count_scan(ctx, js, static_cast<uint64_t*>(S.off.p), g_step(s, 0), S.cws.p);
+      if (e == cudaSuccess && !g.filter)
+        e = claim_output(ctx, cursor, g_step(s, 0), g_step(s, 1), S.ocap, ovf);
+      if (e == cudaSuccess)
+        e = join_write(ctx, js, static_cast<const uint64_t*>(S.off.p), S.ocap, out, 0, cursor,
+                       S.ocap, S.wws.p, S.wbytes, g_step(s, 0), g.filter ? nullptr : g_step(s, 1),
+                       ovf);
+    }
+    for (size_t j = 0; j < grel.size() && e == cudaSuccess; ++j) {
+      GRelRes& G = grel[j];
+      const Relation& R = *rels[G.rel];
+      bool in_b = false;
+      e = radix_sort(ctx, G.plan, G.fresh.out(), G.alt.out(), G.Ucap, G.sort_ws.p, &in_b,
+                     g_cursor(j));
+      const DCols& U = G.sorted_in_alt ? G.alt : G.fresh;
+      DevMerge dm;
+      dm.full = &g_cur()[j].F;
+      dm.n_full = &g_cur()[j].nF;
+      dm.n_fresh = g_cursor(j);
+      dm.delta = reinterpret_cast<const ColsOut*>(&g_next()[j].D);
+      dm.merged = reinterpret_cast<const ColsOut*>(&g_next()[j].F);
+      dm.cap_merged = G.Fcap;
+      dm.overflow = ovf;
+      if (e == cudaSuccess)
+        e = diff_merge(ctx, R.arity, ColsIn{}, G.Fcap, U.in(), G.Ucap, ColsOut{}, ColsOut{},
+                       &g_next()[j].nD, G.merge_ws.p, &dm);
+      if (e == cudaSuccess && opt.n_instances)
+        e = mark_instances(ctx, nullptr, G.Ucap, opt.n_instances,
+                           static_cast<uint64_t*>(inst_last.p), 1, &g_next()[j].D,
+                           &g_next()[j].nD, &g_ctl()->round);
+    }
+    if (e == cudaSuccess)
+      e = round_end(ctx, g_cur(), g_next(), (uint32_t)grel.size(), g_ctl(), g_round(), kGraphRounds,
+                    loop);
+    return e;
+  }
+
+  // Runs rounds on the device until the fixpoint, max_iters or a buffer
+  // overflow; then hands the current versions back to the relations.
+  cdl_status graph_run(uint64_t& round, std::vector<uint64_t>& per_round, uint64_t& iterations,
+                       bool& finished) {
+    finished = false;
+    for (size_t i = 0; i < rels.size(); ++i) {  // room for the current versions
+      const Relation& R = *rels[i];
+      if (!R.idb) continue;
+      gcap_u[i] = std::max<uint64_t>({gcap_u[i], 8 * R.delta.n, 8 * R.fresh.n});
+      gcap_f[i] = std::max<uint64_t>(gcap_f[i], R.full.n + 16 * gcap_u[i]);
+    }
+    cdl_status r = graph_build(round, iterations);
+    if (r == CDL_E_NOMEM || r == CDL_E_CAPACITY) {  // no room for a graph: rounds stay on the host
+      graph_release();
+      cudaGetLastError();
+      graph_ready = false;
+      return CDL_OK;
+    }
+    if (r != CDL_OK) return r;
+    ++g_builds;
+    cudaError_t e = cudaGraphLaunch(gexec, st);
+    GraphCtl ctl{};
+    std::vector<GraphRel> cur(grel.size());
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, g_ctl(), sizeof ctl, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(cur.data(), g_cur(), sizeof(GraphRel) * cur.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    r = fetch(0, 0);  // the error word of every launch
+    if (r != CDL_OK) return r;
+    const uint64_t first = round;
+    if (ctl.round > first) {
+      std::vector<uint64_t> pr(ctl.round - first);
+      e = cudaMemcpy(pr.data(), g_round() + first, 8 * pr.size(), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e, "graph rounds");
+      per_round.insert(per_round.end(), pr.begin(), pr.end());
+    }
+    prof.total_launches += (ctl.round - first + (ctl.done == 2)) * glaunches_per_round;
+    g_rounds += ctl.round - first;
+    round = ctl.round;
+    iterations = ctl.iterations;
+    for (size_t j = 0; j < grel.size(); ++j) {
+      GRelRes& G = grel[j];
+      Relation& R = *rels[G.rel];
+      const int side = cur[j].F.c[0] == G.F[0].c[0] ? 0 : 1;
+      R.full = std::move(G.F[side]);
+      R.full.n = cur[j].nF;
+      R.delta = std::move(G.D[side]);
+      R.delta.n = cur[j].nD;
+      R.version[kFull]++;
+      R.version[kDelta]++;
+    }
+    graph_release();
+    evict_stale();
+    if (ctl.done == 3) return fail(CDL_E_MAXITER, "the fixpoint needs more rounds than max_iters");
+    finished = ctl.done == 1;
+    if (ctl.done == 2)  // a buffer was too small: the next round runs on the host, then larger
+      for (auto& c : gcap_u) c *= 2;
+    if (ctl.done == 2) {
+      for (auto& c : gcap_i) c *= 2;
+      for (size_t i = 0; i < rels.size(); ++i)
+        if (rels[i]->idb) gcap_f[i] = std::max(2 * gcap_f[i], rels[i]->full.n + 16 * gcap_u[i]);
+    }
+    return CDL_OK;
+  }
+
+  // Capacities from the recorded round: room for the sizes seen, many times over.
+  void graph_caps() {
+    gcap_u.assign(rels.size(), 0);
+    gcap_f.assign(rels.size(), 0);
+    gcap_i.assign(grec.size(), 0);
+    std::vector<uint64_t> seen(rels.size(), 0);
+    for (const GStep& g : grec)
+      if (g.last) seen[g.head] += g.seen_total;
+    // option graph >= 2: that many rows at least instead of 2^16 (small
+    // values make later rounds outgrow the buffers, as tests want)
+    const uint64_t floor = opt.graph >= 2 ? (uint64_t)opt.graph : (1u << 16);
+    for (size_t i = 0; i < rels.size(); ++i) {
+      if (!rels[i]->idb) continue;
+      gcap_u[i] = std::max<uint64_t>({8 * seen[i], 8 * rels[i]->delta.n, floor});
+      gcap_f[i] = std::max<uint64_t>(4 * rels[i]->full.n, rels[i]->full.n + 16 * gcap_u[i]);
+    }
+    for (size_t s = 0; s < grec.size(); ++s)
+      gcap_i[s] = std::max<uint64_t>(8 * grec[s].seen_total, floor);
+  }
+
   cdl_status run(cdl_stats* stats) {
     if (ran) return fail(CDL_E_STATE, "cdl_run was already called");
     ran = true;
@@ -1465,10 +1838,15 @@ struct cdl_engine {
         r->ret_cnt.assign(opt.n_instances, 0);
       }
     }
+    grec.clear();
+    grec_bad = graph_ready = false;
+    g_rounds = g_builds = 0;
     for (uint64_t round = 1; status == CDL_OK; ++round) {
       cur_round = round;
       cudaError_t e = cudaSuccess;
+      recording = opt.graph && round == 2;  // the first semi-naive round is the plan
       status = eval_round(round);
+      recording = false;
       if (status != CDL_OK) break;
       for (uint32_t i = 0; i < nr; ++i) {
         Relation& R = *rels[i];
@@ -1530,7 +1908,18 @@ struct cdl_engine {
         status = fail(CDL_E_MAXITER, "the fixpoint needs more rounds than max_iters");
         break;
       }
+      if (opt.graph && round == 2) {
+        graph_ready = graph_plan();
+        if (graph_ready) graph_caps();
+      }
+      if (graph_ready && round >= 2) {  // the next rounds on the device
+        bool finished = false;
+        status = graph_run(round, per_round, iterations, finished);
+        rounds = round;
+        if (status != CDL_OK || finished) break;
+      }
     }
+    graph_release();
     if (opt.n_instances && status == CDL_OK) status = assemble();
     tuner.resolve();
     if (tuner.mode == 2 && !tuner.save() && status == CDL_OK)
@@ -1559,6 +1948,8 @@ struct cdl_engine {
       stats->kernel_launches = prof.total_launches;
       stats->est_predictions = est_pred;
       stats->est_overflows = est_over;
+      stats->graph_rounds = g_rounds;
+      stats->graph_builds = g_builds;
       if (stats->delta_per_round)
         for (uint64_t i = 0; i < per_round.size() && i < stats->delta_cap; ++i)
           stats->delta_per_round[i] = per_round[i];

@@ -29,33 +29,44 @@ constexpr int kJT = 256;  // write pass threads
 constexpr int kJItems = 8;
 constexpr int kJTile = kJT * kJItems;  // merged items per block
 
-__device__ __forceinline__ uint32_t probe_key1(const JoinSpec& j, uint64_t row) {
-  return j.pk1 == 0xFFu ? 0u : __ldg(j.probe.c[j.pk1] + row);
+__device__ __forceinline__ uint32_t probe_key1(const JoinSpec& j, const ColsIn& probe,
+                                              uint64_t row) {
+  return j.pk1 == 0xFFu ? 0u : __ldg(probe.c[j.pk1] + row);
 }
 
 // Range of build rows matching probe row `row`: the hybrid index lookup, or
 // every build row for a join without shared variables.
-__device__ __forceinline__ uint32_t lookup(const JoinSpec& j, uint64_t mask, uint64_t row,
-                                          uint32_t* start) {
+__device__ __forceinline__ uint32_t lookup(const JoinSpec& j, const ColsIn& probe, uint64_t mask,
+                                          uint64_t row, uint32_t* start) {
   if (j.cross) {
     *start = 0;
     return j.n_build;
   }
-  return probe_table(j.table, mask, __ldg(j.probe.c[j.pk0] + row), probe_key1(j, row), start);
+  return probe_table(j.table, mask, __ldg(probe.c[j.pk0] + row), probe_key1(j, probe, row), start);
+}
+
+// The probe side of a launch: the spec's columns and row count, or (inside
+// a captured round) the ones device memory holds, the count clamped to the
+// capacity the spec's n_probe then gives.
+__device__ __forceinline__ ColsIn probe_cols(const JoinSpec& j) {
+  return j.dprobe ? *j.dprobe : j.probe;
 }
 
 __global__ void __launch_bounds__(kCT) k_join_count(const JoinSpec j, uint32_t* __restrict__ counts,
                                                     uint64_t* __restrict__ tile_sums) {
   __shared__ uint64_t red[kCT / 32 + 1];
+  const uint64_t n = dev_size(j.dn, j.n_probe);
+  const ColsIn probe = probe_cols(j);
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  if (base >= n && blockIdx.x > 0) return;
   const uint64_t mask = j.slots - 1;
   uint64_t s = 0;
 #pragma unroll 4
   for (int i = 0; i < kCItems; ++i) {
     const uint64_t row = base + (uint64_t)i * kCT + threadIdx.x;
-    if (row < j.n_probe) {
+    if (row < n) {
       uint32_t st;
-      const uint32_t cnt = lookup(j, mask, row, &st);
+      const uint32_t cnt = lookup(j, probe, mask, row, &st);
       counts[row] = cnt;
       s += cnt;
     }
@@ -70,7 +81,7 @@ __global__ void __launch_bounds__(kCT) k_join_count_only(const JoinSpec j,
   const uint64_t row = (uint64_t)blockIdx.x * kCT + threadIdx.x;
   if (row >= j.n_probe) return;
   uint32_t st;
-  counts[row] = lookup(j, j.slots - 1, row, &st);
+  counts[row] = lookup(j, j.probe, j.slots - 1, row, &st);
 }
 
 // Number of probe rows among the first d items of the merge of the row
@@ -92,16 +103,22 @@ __device__ __forceinline__ uint64_t merge_split(const uint64_t* off, uint64_t n,
 // All blocks' splits at once, one thread per split, so that no block
 // waits on a chain of dependent global loads before its first useful one.
 __global__ void k_write_splits(const uint64_t* __restrict__ off, uint64_t n, uint64_t total,
-                               uint64_t* __restrict__ splits, uint64_t nblocks) {
+                               uint64_t* __restrict__ splits, uint64_t nblocks,
+                               const uint64_t* dn, const uint64_t* dtotal) {
   const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (dn) {  // sizes from device memory (nblocks was sized for the capacities)
+    n = dev_size(dn, n);
+    total = dev_size(dtotal, total);
+    nblocks = (n + total + kJTile - 1) / kJTile;
+  }
   if (b > nblocks) return;
   const uint64_t d = b * kJTile < n + total ? b * kJTile : n + total;
   splits[b] = merge_split(off, n, total, d);
 }
 
-__device__ __forceinline__ uint32_t ref_value(const JoinSpec& j, const Ref& r, uint64_t row,
-                                              uint64_t brow) {
-  if (r.side == 0) return __ldg(j.probe.c[r.v] + row);
+__device__ __forceinline__ uint32_t ref_value(const JoinSpec& j, const ColsIn& probe, const Ref& r,
+                                              uint64_t row, uint64_t brow) {
+  if (r.side == 0) return __ldg(probe.c[r.v] + row);
   if (r.side == 1) return __ldg(j.build.c[r.v] + brow);
   return r.v;
 }
@@ -111,22 +128,30 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
                                                     uint64_t total, ColsOut out, uint64_t base,
                                                     unsigned long long* cursor, uint64_t out_cap,
                                                     const uint64_t* __restrict__ splits,
-                                                    uint32_t* err) {
+                                                    uint32_t* err, const uint64_t* dtotal,
+                                                    const uint64_t* dbase) {
   __shared__ uint64_t s_off[kJTile + 1];
   __shared__ uint32_t s_start[kJTile + 1];
   __shared__ uint64_t s_split[2];
   __shared__ uint32_t red[kJT / 32 + 1];
   __shared__ unsigned long long s_base;
-  const uint64_t nm = j.n_probe + total;
+  const uint64_t n_probe = dev_size(j.dn, j.n_probe);
+  const ColsIn probe = probe_cols(j);
+  total = dev_size(dtotal, total);
+  if (dbase) base = *dbase;
+  const uint64_t nm = n_probe + total;
   const uint64_t d0 = (uint64_t)blockIdx.x * kJTile;
+  if (d0 >= nm) return;  // beyond a device-given size
   const uint64_t d1 = d0 + kJTile < nm ? d0 + kJTile : nm;
   if (splits) {
     if (threadIdx.x < 2) s_split[threadIdx.x] = splits[blockIdx.x + threadIdx.x];
   } else {
-    if (threadIdx.x == 0) s_split[0] = merge_split(off, j.n_probe, total, d0);
-    if (threadIdx.x == 32) s_split[1] = merge_split(off, j.n_probe, total, d1);
+    if (threadIdx.x == 0) s_split[0] = merge_split(off, n_probe, total, d0);
+    if (threadIdx.x == 32) s_split[1] = merge_split(off, n_probe, total, d1);
   }
-  if (!FILTER && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(cursor, (unsigned long long)total);
+  // (a device-sized launch had its claim made by claim_output)
+  if (!FILTER && !dbase && blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(cursor, (unsigned long long)total);
   __syncthreads();
   const uint64_t j0 = s_split[0], j1 = s_split[1];
   const uint64_t o0 = d0 - j0, o1 = d1 - j1;
@@ -136,9 +161,9 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
   for (uint32_t r = threadIdx.x; r < nrows; r += kJT) {
     const uint64_t row = r_lo + r;
     const uint64_t a = __ldg(off + row);
-    const uint64_t b = row + 1 < j.n_probe ? __ldg(off + row + 1) : total;
+    const uint64_t b = row + 1 < n_probe ? __ldg(off + row + 1) : total;
     uint32_t st = 0;
-    if (b > a) lookup(j, mask, row, &st);
+    if (b > a) lookup(j, probe, mask, row, &st);
     s_off[r] = a;
     s_start[r] = st;
   }
@@ -161,12 +186,14 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
       const uint64_t brow = (uint64_t)s_start[lo] + (o - s_off[lo]);
 #pragma unroll
       for (int k = 0; k < kMaxK; ++k)
-        if (k < (int)j.out_k) vals[k] = ref_value(j, j.out[k], row, brow);
+        if (k < (int)j.out_k) vals[k] = ref_value(j, probe, j.out[k], row, brow);
       if (FILTER) {
         for (uint32_t q = 0; q < j.n_eq; ++q)
-          keep &= ref_value(j, j.eq[q][0], row, brow) == ref_value(j, j.eq[q][1], row, brow);
+          keep &= ref_value(j, probe, j.eq[q][0], row, brow) ==
+                  ref_value(j, probe, j.eq[q][1], row, brow);
         for (uint32_t q = 0; q < j.n_neq; ++q)
-          keep &= ref_value(j, j.neq[q][0], row, brow) != ref_value(j, j.neq[q][1], row, brow);
+          keep &= ref_value(j, probe, j.neq[q][0], row, brow) !=
+                  ref_value(j, probe, j.neq[q][1], row, brow);
       }
     }
     uint64_t pos;
@@ -217,7 +244,7 @@ cudaError_t join_count_scan(Ctx& c, const JoinSpec& j, uint64_t* d_off, uint64_t
     ProfScope p(c, kJoinCount, (keyb + 16.0 + 4.0) * j.n_probe);
     k_join_count<<<(unsigned)tiles, kCT, 0, c.st>>>(j, counts, static_cast<uint64_t*>(scan_ws));
   }
-  return scan_finish(c, counts, j.n_probe, d_off, d_total, scan_ws);
+  return scan_finish(c, counts, j.n_probe, d_off, d_total, scan_ws, j.dn);
 }
 
 // ------------------------------------------------------------ single pass
@@ -247,12 +274,14 @@ __device__ __forceinline__ void warp_emit(const JoinSpec& j, ColsOut out, uint64
     if (valid) {
 #pragma unroll
       for (int k = 0; k < kMaxK; ++k)
-        if (k < (int)j.out_k) vals[k] = ref_value(j, j.out[k], prow, brow0 + o);
+        if (k < (int)j.out_k) vals[k] = ref_value(j, j.probe, j.out[k], prow, brow0 + o);
       if (FILTER) {
         for (uint32_t q = 0; q < j.n_eq; ++q)
-          keep &= ref_value(j, j.eq[q][0], prow, brow0 + o) == ref_value(j, j.eq[q][1], prow, brow0 + o);
+          keep &= ref_value(j, j.probe, j.eq[q][0], prow, brow0 + o) ==
+                  ref_value(j, j.probe, j.eq[q][1], prow, brow0 + o);
         for (uint32_t q = 0; q < j.n_neq; ++q)
-          keep &= ref_value(j, j.neq[q][0], prow, brow0 + o) != ref_value(j, j.neq[q][1], prow, brow0 + o);
+          keep &= ref_value(j, j.probe, j.neq[q][0], prow, brow0 + o) !=
+                  ref_value(j, j.probe, j.neq[q][1], prow, brow0 + o);
       }
     }
     uint64_t pos;
@@ -287,7 +316,7 @@ __global__ void __launch_bounds__(kDirT) k_join_direct(const JoinSpec j, ColsOut
        w += nwarps) {
     const uint64_t row = w * 32 + lane;
     uint32_t st = 0, cnt = 0;
-    if (row < j.n_probe) cnt = lookup(j, mask, row, &st);
+    if (row < j.n_probe) cnt = lookup(j, j.probe, mask, row, &st);
     // a long range becomes chunks of the heavy list
     const bool hv = cnt > kHeavyChunk;
     const uint32_t hmask = __ballot_sync(0xffffffffu, hv);
@@ -356,12 +385,14 @@ __global__ void __launch_bounds__(kDirT) k_join_direct(const JoinSpec j, ColsOut
       if (valid) {
 #pragma unroll
         for (int k = 0; k < kMaxK; ++k)
-          if (k < (int)j.out_k) vals[k] = ref_value(j, j.out[k], prow, brow);
+          if (k < (int)j.out_k) vals[k] = ref_value(j, j.probe, j.out[k], prow, brow);
         if (FILTER) {
           for (uint32_t q = 0; q < j.n_eq; ++q)
-            keep &= ref_value(j, j.eq[q][0], prow, brow) == ref_value(j, j.eq[q][1], prow, brow);
+            keep &= ref_value(j, j.probe, j.eq[q][0], prow, brow) ==
+                    ref_value(j, j.probe, j.eq[q][1], prow, brow);
           for (uint32_t q = 0; q < j.n_neq; ++q)
-            keep &= ref_value(j, j.neq[q][0], prow, brow) != ref_value(j, j.neq[q][1], prow, brow);
+            keep &= ref_value(j, j.probe, j.neq[q][0], prow, brow) !=
+                    ref_value(j, j.probe, j.neq[q][1], prow, brow);
         }
       }
       uint64_t pos;
@@ -428,7 +459,8 @@ size_t join_write_workspace(uint64_t n_probe, uint64_t total) {
 
 cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_t total,
                        ColsOut out, uint64_t base, uint64_t* d_cursor, uint64_t out_cap,
-                       void* ws, size_t ws_bytes) {
+                       void* ws, size_t ws_bytes, const uint64_t* d_total, const uint64_t* d_base,
+                       uint32_t* d_soft_err) {
   if (total == 0 || j.n_probe == 0) return cudaSuccess;
   const uint64_t nm = j.n_probe + total;
   const uint64_t blocks = (nm + kJTile - 1) / kJTile;
@@ -436,8 +468,8 @@ cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_
   uint64_t* splits = nullptr;
   if (ws && ws_bytes >= join_write_workspace(j.n_probe, total)) {
     splits = static_cast<uint64_t*>(ws);
-    k_write_splits<<<(unsigned)((blocks + 1 + 255) / 256), 256, 0, c.st>>>(d_off, j.n_probe, total,
-                                                                          splits, blocks);
+    k_write_splits<<<(unsigned)((blocks + 1 + 255) / 256), 256, 0, c.st>>>(
+        d_off, j.n_probe, total, splits, blocks, j.dn, d_total);
   }
   // per probe row: two offsets, key, re-probed slot, its own head columns;
   // per output: the gathered build columns and the written head columns
@@ -450,12 +482,33 @@ cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_
                        (4.0 * nbuild + 4.0 * j.out_k) * total;
   ProfScope p(c, kJoinWrite, bytes);
   auto* cur = reinterpret_cast<unsigned long long*>(d_cursor);
+  uint32_t* err = d_soft_err ? d_soft_err : c.d_err;
   if (filter)
     k_join_write<true><<<(unsigned)blocks, kJT, 0, c.st>>>(j, d_off, total, out, base, cur, out_cap,
-                                                          splits, c.d_err);
+                                                          splits, err, d_total, d_base);
   else
     k_join_write<false><<<(unsigned)blocks, kJT, 0, c.st>>>(j, d_off, total, out, base, cur,
-                                                           out_cap, splits, c.d_err);
+                                                           out_cap, splits, err, d_total, d_base);
+  return cudaGetLastError();
+}
+
+namespace {
+// One thread: the unfiltered join's output range [*cursor, *cursor + total)
+// is claimed and its start stored; a range past cap raises *overflow.
+__global__ void k_claim(unsigned long long* cursor, const uint64_t* total, uint64_t* base,
+                        uint64_t cap, uint32_t* overflow) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const uint64_t b = *cursor, t = *total;
+  *base = b;
+  *cursor = b + t;
+  if (b + t > cap) atomicOr(overflow, 1u);
+}
+}  // namespace
+
+cudaError_t claim_output(Ctx& c, uint64_t* d_cursor, const uint64_t* d_total, uint64_t* d_base,
+                         uint64_t cap, uint32_t* d_overflow) {
+  k_claim<<<1, 32, 0, c.st>>>(reinterpret_cast<unsigned long long*>(d_cursor), d_total, d_base, cap,
+                              d_overflow);
   return cudaGetLastError();
 }
 

@@ -89,11 +89,13 @@ cudaError_t count_heads(Ctx& c, const uint32_t* k0, const uint32_t* k1, uint64_t
 constexpr int kScanTile = 2048;  // elements per scan tile
 size_t scan_workspace(uint64_t n);
 // out[i] = sum in[0..i); *d_total = sum of all (device pointer, may be null).
+// dn (optional): the actual count in device memory, clamped to n, which
+// then only sizes the grid (a launch inside a captured round).
 cudaError_t exclusive_scan(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out,
-                           uint64_t* d_total, void* ws);
+                           uint64_t* d_total, void* ws, const uint64_t* dn = nullptr);
 // Second half of the scan when ws already holds the sums of kScanTile tiles.
 cudaError_t scan_finish(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* d_total,
-                        void* ws);
+                        void* ws, const uint64_t* dn = nullptr);
 
 // -------------------------------------------------------------------- join
 struct Ref {
@@ -115,6 +117,10 @@ struct JoinSpec {
   Ref eq[4][2];
   uint32_t cross;    // 1: no shared variable, every build row matches
   uint32_t n_build;  // build rows (used by cross joins)
+  // inside a captured round: the probe columns and row count in device
+  // memory (n_probe is then the capacity that sizes the grids); else null
+  const ColsIn* dprobe;
+  const uint64_t* dn;
 };
 size_t join_count_workspace(uint64_t n_probe);
 // Pass 1 alone: counts[i] for every probe row.
@@ -128,9 +134,18 @@ cudaError_t join_count_scan(Ctx& c, const JoinSpec& j, uint64_t* d_off, uint64_t
 // ws (optional, join_write_workspace bytes) holds every block's merge-path
 // split, computed up front; without it each block searches for its own.
 size_t join_write_workspace(uint64_t n_probe, uint64_t total);
+// Inside a captured round: d_total (the join size, total then being its
+// capacity) and d_base (the start claimed by claim_output, unfiltered
+// joins) come from device memory, and a write past out_cap raises
+// *d_soft_err instead of the engine's error word.
 cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_t total,
                        ColsOut out, uint64_t base, uint64_t* d_cursor, uint64_t out_cap,
-                       void* ws, size_t ws_bytes);
+                       void* ws, size_t ws_bytes, const uint64_t* d_total = nullptr,
+                       const uint64_t* d_base = nullptr, uint32_t* d_soft_err = nullptr);
+// *d_base = *d_cursor; *d_cursor += *d_total; *d_overflow = 1 when the range
+// passes cap (one thread).
+cudaError_t claim_output(Ctx& c, uint64_t* d_cursor, const uint64_t* d_total, uint64_t* d_base,
+                         uint64_t cap, uint32_t* d_overflow);
 
 // -------------------------------------------------------------------- sort
 // Digit plan of an LSD radix sort over the packed key of K columns.
@@ -150,18 +165,34 @@ RadixPlan make_radix_plan(uint32_t k, const uint32_t* col_bits, uint32_t digit_b
 size_t radix_workspace(uint64_t n, uint32_t digit_bits, uint32_t threads = 512);
 // Sorts (a, n rows) using b as the alternate buffer; returns in *in_b
 // whether the result ended in b.
+// dn (optional): the row count in device memory, clamped to n, which then
+// only sizes the grids; every pass runs then (none is skipped for one tile).
 cudaError_t radix_sort(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t n, void* ws,
-                       bool* in_b);
+                       bool* in_b, const uint64_t* dn = nullptr);
 // Column maxima into d_max[k] (for plans of unknown data).
 cudaError_t column_max(Ctx& c, ColsIn in, uint32_t k, uint64_t n, uint32_t* d_max);
 
 // ------------------------------------------------------------------ setops
 size_t diff_merge_workspace(uint64_t n_full, uint64_t n_fresh);
+// A diff_merge inside a captured round: Full's columns and size, the new
+// tuples' count and the output columns are read from device memory (n_full
+// and n_fresh then only size the grids and clamp the counts).  When |full| +
+// |new| exceeds cap_merged nothing is written, |delta| = 0 and *overflow is
+// raised.
+struct DevMerge {
+  const ColsIn* full = nullptr;
+  const uint64_t* n_full = nullptr;
+  const uint64_t* n_fresh = nullptr;
+  const ColsOut* delta = nullptr;
+  const ColsOut* merged = nullptr;
+  uint64_t cap_merged = 0;
+  uint32_t* overflow = nullptr;
+};
 // delta = fresh - full, merged = full U delta; *d_ndelta receives |delta|.
 // When merged.c[0] is null only delta is produced.
 cudaError_t diff_merge(Ctx& c, uint32_t k, ColsIn full, uint64_t n_full, ColsIn fresh,
                        uint64_t n_fresh, ColsOut delta, ColsOut merged, uint64_t* d_ndelta,
-                       void* ws);
+                       void* ws, const DevMerge* dm = nullptr);
 
 // Selection + projection of one atom: keeps rows with col == const, col ==
 // col and (on output refs) out != out; writes out tuples packed at
@@ -187,8 +218,35 @@ cudaError_t select_project(Ctx& c, const SelectSpec& s, ColsOut out, uint64_t* d
 
 // last_round[v] = round for every instance id v < n_instances present in the
 // sorted instance column inst (n rows).
+// Inside a captured round (dinst non-null): column 0 of *dinst, the count
+// *dn (clamped to n) and round + *dround.
 cudaError_t mark_instances(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,
-                           uint64_t* last_round, uint64_t round);
+                           uint64_t* last_round, uint64_t round, const ColsIn* dinst = nullptr,
+                           const uint64_t* dn = nullptr, const uint64_t* dround = nullptr);
+
+// ------------------------------------------------------- captured rounds
+// Device state of one derived relation in a round captured as a CUDA graph:
+// its full and delta versions and their sizes.  A round reads cur and
+// writes next; the round's last kernel swaps them.
+struct GraphRel {
+  ColsIn F, D;
+  uint64_t nF, nD;
+};
+struct GraphCtl {
+  uint64_t round;       // rounds completed (all launches, numbered as the engine does)
+  uint64_t iterations;  // last round that derived a tuple
+  uint64_t done;        // 0 running, 1 fixpoint, 2 a buffer overflowed, 3 past max_iters
+  uint64_t max_iters;   // 0: no limit
+  uint32_t overflow;    // raised by any launch of the round that ran out of room
+  uint32_t pad;
+};
+// The round's last kernel (one thread): on overflow nothing moves and the
+// loop stops (cur still holds the last complete round); else next.nF =
+// cur.nF + next.nD, per_round[round] = sum of next.nD, cur <-> next, and the
+// loop's condition is set to continue while the round derived something.
+cudaError_t round_end(Ctx& c, GraphRel* cur, GraphRel* next, uint32_t nrel, GraphCtl* ctl,
+                      uint64_t* per_round, uint64_t per_round_cap,
+                      cudaGraphConditionalHandle loop);
 // bounds[i] (i = 0..n_instances) = first row of the sorted column inst whose
 // value is >= i: instance i occupies rows [bounds[i], bounds[i + 1]).
 cudaError_t instance_bounds(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,

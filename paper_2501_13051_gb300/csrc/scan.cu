@@ -17,9 +17,12 @@ __host__ __device__ constexpr uint32_t pad_idx(uint32_t i) { return i + (i >> 5)
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in,
                                                               uint64_t n,
-                                                              uint64_t* __restrict__ tile_sums) {
+                                                              uint64_t* __restrict__ tile_sums,
+                                                              const uint64_t* dn) {
   __shared__ uint64_t red[kScanThreads / 32 + 1];
+  n = dev_size(dn, n);
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  if (base >= n && blockIdx.x > 0) return;  // beyond a device-given size
   uint64_t s = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
@@ -31,11 +34,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
-// One block: exclusive scan of ntiles tile sums in place; total -> *d_total.
-__global__ void __launch_bounds__(kTopThreads) k_scan_top(uint64_t* __restrict__ sums,
-                                                          uint64_t ntiles,
-                                                          uint64_t* __restrict__ d_total) {
+// One block: exclusive scan of the tile sums of n items in place; total ->
+// *d_total.
+__global__ void __launch_bounds__(kTopThreads) k_scan_top(uint64_t* __restrict__ sums, uint64_t n,
+                                                          uint64_t* __restrict__ d_total,
+                                                          const uint64_t* dn) {
   __shared__ uint64_t red[kTopThreads / 32 + 1];
+  const uint64_t ntiles = (dev_size(dn, n) + kScanTile - 1) / kScanTile;
   uint64_t carry = 0;
   for (uint64_t b = 0; b < ntiles; b += kTopThreads) {
     const uint64_t i = b + threadIdx.x;
@@ -51,10 +56,13 @@ __global__ void __launch_bounds__(kTopThreads) k_scan_top(uint64_t* __restrict__
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ in,
                                                              uint64_t n,
                                                              const uint64_t* __restrict__ prefix,
-                                                             uint64_t* __restrict__ out) {
+                                                             uint64_t* __restrict__ out,
+                                                             const uint64_t* dn) {
   __shared__ uint32_t s_in[pad_idx(kScanTile) + 1];
   __shared__ uint64_t red[kScanThreads / 32 + 1];
+  n = dev_size(dn, n);
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  if (base >= n) return;
   // striped, coalesced load into shared memory
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
@@ -87,8 +95,10 @@ constexpr uint64_t kSmallScan = 1 << 16;
 
 __global__ void __launch_bounds__(kTopThreads) k_scan_small(const uint32_t* __restrict__ in,
                                                             uint64_t n, uint64_t* __restrict__ out,
-                                                            uint64_t* __restrict__ d_total) {
+                                                            uint64_t* __restrict__ d_total,
+                                                            const uint64_t* dn) {
   __shared__ uint64_t red[kTopThreads / 32 + 1];
+  n = dev_size(dn, n);
   constexpr int kI = 4;
   uint64_t carry = 0;
   for (uint64_t b = 0; b < n; b += (uint64_t)kTopThreads * kI) {
@@ -120,36 +130,36 @@ size_t scan_workspace(uint64_t n) {
 }
 
 cudaError_t exclusive_scan(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out,
-                           uint64_t* d_total, void* ws) {
+                           uint64_t* d_total, void* ws, const uint64_t* dn) {
   if (n == 0) {
     if (d_total) return cudaMemsetAsync(d_total, 0, sizeof(uint64_t), c.st);
     return cudaSuccess;
   }
-  if (n <= kSmallScan) return scan_finish(c, in, n, out, d_total, ws);
+  if (n <= kSmallScan) return scan_finish(c, in, n, out, d_total, ws, dn);
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
   uint64_t* sums = static_cast<uint64_t*>(ws);
   {
     ProfScope p(c, kScan, 4.0 * n);
-    k_scan_reduce<<<(unsigned)tiles, kScanThreads, 0, c.st>>>(in, n, sums);
+    k_scan_reduce<<<(unsigned)tiles, kScanThreads, 0, c.st>>>(in, n, sums, dn);
   }
-  return scan_finish(c, in, n, out, d_total, ws);
+  return scan_finish(c, in, n, out, d_total, ws, dn);
 }
 
 cudaError_t scan_finish(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* d_total,
-                        void* ws) {
+                        void* ws, const uint64_t* dn) {
   if (n == 0) {
     if (d_total) return cudaMemsetAsync(d_total, 0, sizeof(uint64_t), c.st);
     return cudaSuccess;
   }
   ProfScope p(c, kScan, 4.0 * n + 8.0 * n);
   if (n <= kSmallScan) {  // tile sums, if any were stored, are not needed
-    k_scan_small<<<1, kTopThreads, 0, c.st>>>(in, n, out, d_total);
+    k_scan_small<<<1, kTopThreads, 0, c.st>>>(in, n, out, d_total, dn);
     return cudaGetLastError();
   }
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
   uint64_t* sums = static_cast<uint64_t*>(ws);
-  k_scan_top<<<1, kTopThreads, 0, c.st>>>(sums, tiles, d_total);
-  k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, c.st>>>(in, n, sums, out);
+  k_scan_top<<<1, kTopThreads, 0, c.st>>>(sums, n, d_total, dn);
+  k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, c.st>>>(in, n, sums, out, dn);
   return cudaGetLastError();
 }
 

@@ -78,7 +78,13 @@ __global__ void k_check_values(ColsIn in, uint32_t k, uint64_t n, uint32_t* d_ma
 // something in this round.
 __global__ void k_mark_instances(const uint32_t* __restrict__ inst, uint64_t n,
                                  uint32_t n_instances, uint64_t* __restrict__ last_round,
-                                 uint64_t round) {
+                                 uint64_t round, const ColsIn* dinst, const uint64_t* dn,
+                                 const uint64_t* dround) {
+  if (dinst) {  // inside a captured round: the delta and the round from device memory
+    inst = dinst->c[0];
+    n = dev_size(dn, n);
+    round += *dround;
+  }
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t v = __ldg(inst + i);
@@ -166,11 +172,12 @@ cudaError_t gather_segments(Ctx& c, uint32_t k, ColsIn a, ColsIn b, const uint64
 }
 
 cudaError_t mark_instances(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,
-                           uint64_t* last_round, uint64_t round) {
+                           uint64_t* last_round, uint64_t round, const ColsIn* dinst,
+                           const uint64_t* dn, const uint64_t* dround) {
   if (n == 0) return cudaSuccess;
   ProfScope p(c, kMisc, 4.0 * n);
   k_mark_instances<<<(unsigned)((n + 255) / 256), 256, 0, c.st>>>(inst, n, n_instances, last_round,
-                                                                  round);
+                                                                  round, dinst, dn, dround);
   return cudaGetLastError();
 }
 

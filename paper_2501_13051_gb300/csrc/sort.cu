@@ -37,9 +37,14 @@ __device__ __forceinline__ uint32_t digit_of(const uint32_t (&v)[K], const PassP
 template <int K, int BITS, int T>
 __global__ void __launch_bounds__(T) k_radix_upsweep(ColsIn in, uint64_t n, PassP p,
                                                      uint32_t* __restrict__ tile_hist,
-                                                     uint64_t ntiles) {
+                                                     uint64_t ntiles, const uint64_t* dn) {
   constexpr int R = 1 << BITS;
   constexpr int kRT = T, kRTile = T * kRItems;
+  if (dn) {  // device-given size: the grid covers the capacity
+    n = dev_size(dn, n);
+    ntiles = (n + kRTile - 1) / kRTile;
+    if (blockIdx.x >= ntiles) return;
+  }
   __shared__ uint32_t h[R];
   for (int i = threadIdx.x; i < R; i += kRT) h[i] = 0;
   __syncthreads();
@@ -66,9 +71,14 @@ template <int K, int BITS, int T>
 __global__ void __launch_bounds__(T, 1536 / T) k_radix_scatter(ColsIn in, ColsOut out, uint64_t n,
                                                              PassP p,
                                                              const uint64_t* __restrict__ off,
-                                                             uint64_t ntiles) {
+                                                             uint64_t ntiles, const uint64_t* dn) {
   constexpr int R = 1 << BITS;
   constexpr int kRT = T, kRTile = T * kRItems, kRW = T / 32;
+  if (dn) {  // device-given size: the grid covers the capacity
+    n = dev_size(dn, n);
+    ntiles = (n + kRTile - 1) / kRTile;
+    if (blockIdx.x >= ntiles) return;
+  }
   constexpr int DPT = (R + kRT - 1) / kRT;
   __shared__ uint32_t wh[kRW][R];  // per-warp digit counts, then per-warp offsets
   __shared__ uint32_t tstart[R];   // tile-local start of each digit's run
@@ -175,9 +185,15 @@ __global__ void k_column_max(ColsIn in, uint32_t k, uint64_t n, uint32_t* d_max)
   }
 }
 
+// R x tiles of the device-given size: the length of the digit-major count
+// array the pass's scan covers.
+__global__ void k_cells(const uint64_t* dn, uint64_t cap, uint64_t tile, uint64_t R, uint64_t* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = R * ((dev_size(dn, cap) + tile - 1) / tile);
+}
+
 template <int K, int BITS, int T>
 cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t n, void* ws,
-                        bool* in_b) {
+                        bool* in_b, const uint64_t* dn) {
   constexpr int R = 1 << BITS;
   constexpr int kRT = T, kRTile = T * kRItems;
   const uint64_t ntiles = (n + kRTile - 1) / kRTile;
@@ -186,6 +202,11 @@ cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uin
   uint64_t* off = reinterpret_cast<uint64_t*>(static_cast<char*>(ws) +
                                               ((cells * 4 + 255) & ~uint64_t(255)));
   void* scan_ws = reinterpret_cast<char*>(off) + ((cells * 8 + 255) & ~uint64_t(255));
+  uint64_t* d_cells = nullptr;  // device-sized: scan length, after the scan's workspace
+  if (dn) {
+    d_cells = reinterpret_cast<uint64_t*>(static_cast<char*>(scan_ws) + scan_workspace(cells));
+    k_cells<<<1, 32, 0, c.st>>>(dn, n, kRTile, R, d_cells);
+  }
   const size_t smem = sizeof(uint32_t) * K * kRTile;
   cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<K, BITS, T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -207,19 +228,19 @@ cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uin
     uint32_t cols_used = 0;
     for (int k = 0; k < K; ++k) cols_used += p.mask[k] != 0;
     // one tile: its own ranking is the global order, no histogram pass
-    const bool single = ntiles == 1;
+    const bool single = ntiles == 1 && !dn;
     if (!single) {
       {
         ProfScope ps(c, kRadixUpsweep, 4.0 * cols_used * n + 4.0 * cells);
-        k_radix_upsweep<K, BITS, T><<<(unsigned)ntiles, kRT, 0, c.st>>>(in, n, p, hist, ntiles);
+        k_radix_upsweep<K, BITS, T><<<(unsigned)ntiles, kRT, 0, c.st>>>(in, n, p, hist, ntiles, dn);
       }
-      e = exclusive_scan(c, hist, cells, off, nullptr, scan_ws);
+      e = exclusive_scan(c, hist, cells, off, nullptr, scan_ws, d_cells);
       if (e != cudaSuccess) return e;
     }
     {
       ProfScope ps(c, kRadixScatter, 8.0 * K * n);
       k_radix_scatter<K, BITS, T><<<(unsigned)ntiles, kRT, smem, c.st>>>(
-          in, dst, n, p, single ? nullptr : off, ntiles);
+          in, dst, n, p, single ? nullptr : off, ntiles, dn);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -232,15 +253,15 @@ cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uin
 
 template <int K>
 cudaError_t sort_k(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t n, void* ws,
-                   bool* in_b) {
+                   bool* in_b, const uint64_t* dn) {
   const bool wide = plan.threads == 512;
   switch (plan.bits) {
     case 8:
-      return wide ? sort_passes<K, 8, 512>(c, plan, a, b, n, ws, in_b)
-                  : sort_passes<K, 8, 256>(c, plan, a, b, n, ws, in_b);
+      return wide ? sort_passes<K, 8, 512>(c, plan, a, b, n, ws, in_b, dn)
+                  : sort_passes<K, 8, 256>(c, plan, a, b, n, ws, in_b, dn);
     case 10:
-      return wide ? sort_passes<K, 10, 512>(c, plan, a, b, n, ws, in_b)
-                  : sort_passes<K, 10, 256>(c, plan, a, b, n, ws, in_b);
+      return wide ? sort_passes<K, 10, 512>(c, plan, a, b, n, ws, in_b, dn)
+                  : sort_passes<K, 10, 256>(c, plan, a, b, n, ws, in_b, dn);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -283,18 +304,18 @@ size_t radix_workspace(uint64_t n, uint32_t digit_bits, uint32_t threads) {
   const uint64_t ntiles = (n + tile - 1) / tile;
   const uint64_t cells = R * ntiles;
   return ((cells * 4 + 255) & ~uint64_t(255)) + ((cells * 8 + 255) & ~uint64_t(255)) +
-         scan_workspace(cells);
+         scan_workspace(cells) + 256;
 }
 
 cudaError_t radix_sort(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t n, void* ws,
-                       bool* in_b) {
+                       bool* in_b, const uint64_t* dn) {
   *in_b = false;
-  if (n <= 1 || plan.npass == 0) return cudaSuccess;
+  if ((n <= 1 && !dn) || n == 0 || plan.npass == 0) return cudaSuccess;
   switch (plan.k) {
-    case 1: return sort_k<1>(c, plan, a, b, n, ws, in_b);
-    case 2: return sort_k<2>(c, plan, a, b, n, ws, in_b);
-    case 3: return sort_k<3>(c, plan, a, b, n, ws, in_b);
-    case 4: return sort_k<4>(c, plan, a, b, n, ws, in_b);
+    case 1: return sort_k<1>(c, plan, a, b, n, ws, in_b, dn);
+    case 2: return sort_k<2>(c, plan, a, b, n, ws, in_b, dn);
+    case 3: return sort_k<3>(c, plan, a, b, n, ws, in_b, dn);
+    case 4: return sort_k<4>(c, plan, a, b, n, ws, in_b, dn);
     default: return cudaErrorInvalidValue;
   }
 }

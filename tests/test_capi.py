@@ -46,4 +46,4 @@ def test_structs_match_header_sizes():
     assert ctypes.sizeof(cdl.Term) == 8
     assert ctypes.sizeof(cdl.ColRef) == 8
     assert ctypes.sizeof(cdl.Atom) == 16
-    assert ctypes.sizeof(cdl.Stats) == 8 * 12
+    assert ctypes.sizeof(cdl.Stats) == 8 * 14
