@@ -174,18 +174,20 @@ __device__ __forceinline__ uint32_t co_rank(const ColsIn& F, const ColsIn& U, co
   return rep ? kRepeat : p;
 }
 
-// Persistent over groups of eight tiles (grid = resident blocks).  Each warp
-// takes one tile of the group: a tile without New tuples costs one store, a
-// sparse one (New < Full / 16) is searched by its warp alone with cached
-// global loads; dense tiles are then taken by the whole block, which stages
-// their Full slice in shared memory.  So a round whose few new tuples meet a
-// large Full keeps every warp busy instead of one block per tile.
+// Persistent over groups of `group` tiles (1..8; grid = resident blocks).
+// Warp w takes tile w of the group: a tile without New tuples costs one
+// store, a sparse one (New < Full / 16) is searched by its warp alone with
+// cached global loads; dense tiles are then taken by the whole block, which
+// stages their Full slice in shared memory.  So a round whose few new tuples
+// meet a large Full keeps every warp busy instead of one block per tile,
+// while a small merge (fewer tiles than eight per resident block) keeps one
+// tile per block.
 template <int K>
 __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t nF, uint64_t nU,
                                                    const uint64_t* __restrict__ splits,
                                                    uint32_t* __restrict__ corank,
                                                    uint32_t* __restrict__ tile_cnt,
-                                                   uint64_t ntiles, DevMerge dm) {
+                                                   uint64_t ntiles, DevMerge dm, uint32_t group) {
   extern __shared__ uint32_t s[];  // K x kDTile: the Full slice of a dense tile
   if (!resolve(dm, F, nF, nU, ntiles)) return;
   __shared__ uint32_t red[kDT / 32 + 1];
@@ -193,11 +195,11 @@ __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t 
   __shared__ uint32_t dense[kW];
   __shared__ uint32_t n_dense;
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-  for (uint64_t g = blockIdx.x; g * kW < ntiles; g += gridDim.x) {
+  for (uint64_t g = blockIdx.x; g * group < ntiles; g += gridDim.x) {
     if (threadIdx.x == 0) n_dense = 0;
     __syncthreads();
-    const uint64_t tile = g * kW + warp;
-    if (tile < ntiles) {
+    const uint64_t tile = g * group + warp;
+    if (warp < group && tile < ntiles) {
       const uint64_t d0 = tile * kDTile;
       const uint64_t d1 = d0 + kDTile < nF + nU ? d0 + kDTile : nF + nU;
       const uint64_t a0 = splits[tile], a1 = splits[tile + 1];
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t 
     __syncthreads();
     const uint32_t nd = n_dense;
     for (uint32_t q = 0; q < nd; ++q) {
-      const uint64_t t = g * kW + dense[q];
+      const uint64_t t = g * group + dense[q];
       const uint64_t d0 = t * kDTile;
       const uint64_t d1 = d0 + kDTile < nF + nU ? d0 + kDTile : nF + nU;
       const uint64_t a0 = splits[t], a1 = splits[t + 1];
@@ -410,15 +412,19 @@ cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, u
     if (e != cudaSuccess) return e;
     resident = (per_sm > 0 ? per_sm : 1) * sms;
   }
-  const uint64_t groups = (tiles + kDT / 32 - 1) / (kDT / 32);  // eight tiles per group
+  // tiles per group: eight once there are eight per resident block, else
+  // fewer, down to one per block for small merges
+  uint64_t group = tiles / (uint64_t)resident;
+  group = group < 1 ? 1 : (group > (uint64_t)(kDT / 32) ? (uint64_t)(kDT / 32) : group);
+  const uint64_t groups = (tiles + group - 1) / group;
   const uint64_t count_grid = groups < (uint64_t)resident ? groups : (uint64_t)resident;
   {
     // New read, co-ranks written; Full sectors are read only where touched
     ProfScope p(c, kDiffCount, (4.0 * K + 4.0) * n_fresh);
     k_merge_splits<K><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, c.st>>>(
         full, n_full, fresh, n_fresh, splits, tiles, dm);
-    k_count_new<K><<<(unsigned)count_grid, kDT, smem_count, c.st>>>(full, fresh, n_full, n_fresh,
-                                                                     splits, corank, cnt, tiles, dm);
+    k_count_new<K><<<(unsigned)count_grid, kDT, smem_count, c.st>>>(
+        full, fresh, n_full, n_fresh, splits, corank, cnt, tiles, dm, (uint32_t)group);
   }
   e = exclusive_scan(c, cnt, tiles, pre, d_ndelta, scan_ws, d_tiles);
   if (e != cudaSuccess) return e;
