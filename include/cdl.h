@@ -91,7 +91,8 @@ typedef struct {
   uint32_t radix_bits; /* radix digit width 8 or 10; 0 = default 8 */
   const char* log_path; /* reserved, must be NULL */
   double est_margin;   /* predicted buffers hold 2^(prediction + est_margin) tuples;
-                          0 = default 1.0 (negative values force fallbacks in tests) */
+                          0 = default 1.0 (negative values force fallbacks in tests); every
+                          fallback of a run adds 0.5 for the rest of the run, up to 4 */
   uint32_t n_instances; /* > 0: batched independent fixpoints.  Column 0 of every
                            relation holds an instance id < n_instances (CDL_E_VALUE at
                            cdl_run otherwise) and every rule has one variable in column 0

@@ -342,7 +342,8 @@ struct cdl_engine {
   DBuf est_w, est_wb, est_io;  // FP32 and BF16 parameters; features + prediction
   float* h_est = nullptr;      // pinned host mirror of est_io
   bool est_weights = false;
-  double est_margin = 1.0;
+  double est_margin = 1.0;  // the configured margin (log2 units)
+  double est_boost = 0.0;   // added after each overrun of this run, up to 4
   uint64_t est_pred = 0, est_over = 0;
   uint64_t cur_round = 0;
   std::vector<float> log_x, log_y;
@@ -1021,7 +1022,8 @@ struct cdl_engine {
         if (r != CDL_OK) return r;
         note_cursors();
         if (last && rels[rule.head.rel]->fresh_overflow) return CDL_OK;  // redone exact
-        const double want = std::exp2(std::min(40.0, (double)h_est[kMlpIn] + est_margin));
+        const double want =
+            std::exp2(std::min(40.0, (double)h_est[kMlpIn] + est_margin + est_boost));
         // a large predicted join keeps the count pass: next to its write the
         // count is cheap, while an overflow would cost the whole round
         if (want <= kDirectMaxTuples) {
@@ -1458,6 +1460,8 @@ struct cdl_engine {
     }
     if (!any) return CDL_OK;
     force_exact = true;
+    // each overrun widens this run's later predictions by half a step (x 1.41)
+    est_boost = std::min(4.0, est_boost + 0.5);
     for (uint32_t i = 0; i < nr; ++i)
       if (redo[i]) {
         ++est_over;
@@ -1814,6 +1818,7 @@ struct cdl_engine {
     cdl_status status = CDL_OK;
     const uint32_t nr = (uint32_t)rels.size();
     est_pred = est_over = 0;
+    est_boost = 0.0;
     if (opt.estimator >= 1) {
       constexpr uint64_t kHeavyCap = 1 << 20;  // chunks of 2048 outputs: 2^31 outputs
       join_sizes = alloc(8 * kMaxDeferred);
