@@ -132,3 +132,20 @@ def test_export_capacity(cdl):
         st = cdl.lib().cdl_relation_export(eng._h, eng.rels["r"], cdl._ptrs([buf.ctypes.data]), 4,
                                            ctypes.byref(got), 0)
         assert st == -3 and got.value == 10
+
+
+def test_export_to_pinned_memory_in_chunks(cdl):
+    # > 64 MB of columns: the export to pinned host memory is split into
+    # chunks over several streams; it must equal the pageable export
+    import torch
+    prog = W.sg_program(W.random_forest(20000, 41))
+    with cdl.Engine() as e:
+        e.load_program(prog)
+        e.run()
+        n = e.size("sg")
+        assert n * 8 > (64 << 20)
+        pinned = [torch.empty(n, dtype=torch.int32, pin_memory=True) for _ in range(2)]
+        e.export("sg", out=[t.data_ptr() for t in pinned])
+        want = e.export("sg")
+    got = np.stack([t.numpy().view(np.uint32) for t in pinned], 1)
+    assert np.array_equal(got, want)
