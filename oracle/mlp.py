@@ -2,7 +2,7 @@
 
 Only tests import this module.  It shares no code with the GPU library.
 
-The network (an addition of this build; the paper has no learned part)
+The network (not in the paper, which has no learned part)
 maps 16 join features to a prediction of log2(1 + join output size):
     h1 = relu(W1 x + b1)      W1: 64 x 16
     h2 = relu(W2 h1 + b2)     W2: 64 x 64
