@@ -107,6 +107,8 @@ typedef struct {
                            the results back to tune_cache at the end of cdl_run.  Results
                            never depend on it */
   const char* tune_cache; /* tuner file path (copied at cdl_create), or NULL: in memory */
+  uint64_t est_min_rows; /* joins with fewer probe rows keep the count pass (the estimator
+                           skips them: there the pass is cheap); 0 = default 32768 */
   int32_t graph;        /* 1: after the first semi-naive round, run the rounds of a program
                            whose rules each join one derived atom with input relations as
                            one CUDA graph: the round captured once, repeated by a device-side

@@ -353,6 +353,7 @@ struct cdl_engine {
   // to the end of the round: their sizes land in join_sizes[i]
   static constexpr uint32_t kMaxDeferred = 4096;
   static constexpr double kDirectMaxTuples = double(1 << 24);
+  static constexpr uint64_t kPredictMinRows = 1 << 15;  // smaller probes keep the count pass
   struct Deferred {
     std::tuple<size_t, size_t, size_t> step;
     uint32_t head = 0;  // relation the join appends to
@@ -1009,7 +1010,10 @@ struct cdl_engine {
       const bool filter = js.n_neq > 0 || js.n_eq > 0;
       // features of this join, for the estimator's prediction and its log
       const std::tuple<size_t, size_t, size_t> step_key{(size_t)(&rule - rules.data()), start, t};
-      const bool feats = ix != nullptr && (est_ready() || opt.estimator >= 2);
+      // a prediction pays off where the count pass it saves is not trivial
+      const bool predict = ix != nullptr && est_ready() && !force_exact &&
+                           P.n >= (opt.est_min_rows ? opt.est_min_rows : kPredictMinRows);
+      const bool feats = ix != nullptr && (predict || opt.estimator >= 2);
       if (feats) {
         const Relation* PR = P.rel >= 0 ? rels[P.rel].get() : nullptr;
         const auto po = prev_out.find(step_key);
@@ -1020,7 +1024,7 @@ struct cdl_engine {
         cudaError_t e = join_features(ctx, P.c[js.pk0], js.pk1 == 0xFFu ? nullptr : P.c[js.pk1],
                                       P.n, ix->cols[hkey[0]],
                                       hkey.size() > 1 ? ix->cols[hkey[1]] : nullptr, B.n, hf, io);
-        if (e == cudaSuccess && est_ready())
+        if (e == cudaSuccess && predict)
           e = mlp_infer_bf16(ctx, est_wb.p, io, 1, io + kMlpIn);
         if (e == cudaSuccess)
           e = cudaMemcpyAsync(h_est, io, sizeof(float) * (kMlpIn + 1), cudaMemcpyDeviceToHost, st);
@@ -1033,7 +1037,7 @@ struct cdl_engine {
         log_y.push_back((float)std::log2(1.0 + (double)size));
       };
       bool predicted = false;
-      if (feats && est_ready() && !force_exact) {
+      if (predict) {
         // single pass into a buffer sized by the prediction
         r = fetch(kSlotScratch, kSlotCursor + (uint32_t)rels.size() - kSlotScratch);
         if (r != CDL_OK) return r;

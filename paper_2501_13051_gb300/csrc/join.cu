@@ -249,11 +249,12 @@ cudaError_t join_count_scan(Ctx& c, const JoinSpec& j, uint64_t* d_off, uint64_t
 
 // ------------------------------------------------------------ single pass
 // The write without count and scan, for joins sized by the estimator: a
-// warp takes 32 probe rows, scans their range lengths with shuffles, claims
-// their outputs with one atomic on the cursor and writes them together
-// (lane l writes outputs l, l + 32, ...; the row of an output is found by a
-// five-step search over the warp's offsets), so a hot key is written by 32
-// lanes rather than one.
+// block takes 256 probe rows at a time, scans their range lengths in shared
+// memory, claims the rows' outputs with one atomic on the cursor and writes
+// them together -- thread t writes outputs t, t + 256, ..., each finding its
+// row by binary search over the block's offsets, as the exact write does.
+// A row with more than kHeavyChunk outputs goes to the heavy list instead,
+// so a hot key never holds one block.
 constexpr int kDirT = 256;
 
 // Writes the outputs [o_begin, o_end) of probe row prow (build rows from
@@ -308,81 +309,70 @@ __global__ void __launch_bounds__(kDirT) k_join_direct(const JoinSpec j, ColsOut
                                                        unsigned long long* cursor, uint64_t cap,
                                                        unsigned long long* total,
                                                        uint32_t* overflow, HeavyList heavy) {
-  const uint32_t lane = lane_id();
-  const uint32_t lt = lanemask_lt();
+  __shared__ uint32_t s_off[kDirT];    // block-local exclusive offsets of the rows
+  __shared__ uint32_t s_start[kDirT];  // first build row of each row's range
+  __shared__ uint32_t red[kDirT / 32 + 1];
+  __shared__ unsigned long long s_base;
   const uint64_t mask = j.slots - 1;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * kDirT) >> 5;
-  for (uint64_t w = ((uint64_t)blockIdx.x * kDirT + threadIdx.x) >> 5; w * 32 < j.n_probe;
-       w += nwarps) {
-    const uint64_t row = w * 32 + lane;
+  for (uint64_t b0 = (uint64_t)blockIdx.x * kDirT; b0 < j.n_probe;
+       b0 += (uint64_t)gridDim.x * kDirT) {
+    const uint64_t row = b0 + threadIdx.x;
     uint32_t st = 0, cnt = 0;
     if (row < j.n_probe) cnt = lookup(j, j.probe, mask, row, &st);
-    // a long range becomes chunks of the heavy list
-    const bool hv = cnt > kHeavyChunk;
-    const uint32_t hmask = __ballot_sync(0xffffffffu, hv);
-    if (hmask) {
-      if (hv) {
-        atomicAdd(total, (unsigned long long)cnt);
-        uint64_t out0 = 0;
-        bool ok = true;
-        if (!FILTER) {
-          out0 = atomicAdd(cursor, (unsigned long long)cnt);
-          ok = out0 + cnt <= cap;
+    if (cnt > kHeavyChunk) {  // a long range becomes chunks of the heavy list
+      atomicAdd(total, (unsigned long long)cnt);
+      uint64_t out0 = 0;
+      bool ok = true;
+      if (!FILTER) {
+        out0 = atomicAdd(cursor, (unsigned long long)cnt);
+        ok = out0 + cnt <= cap;
+      }
+      const uint32_t nch = (cnt + kHeavyChunk - 1) / kHeavyChunk;
+      const uint64_t at = ok ? atomicAdd((unsigned long long*)heavy.n, (unsigned long long)nch) : 0;
+      ok &= at + nch <= heavy.cap;
+      if (ok) {
+        for (uint32_t q = 0; q < nch; ++q) {
+          HeavyChunk h;
+          h.prow = row;
+          h.out0 = out0 + (uint64_t)q * kHeavyChunk;
+          h.brow = st + q * kHeavyChunk;
+          h.len = q + 1 < nch ? kHeavyChunk : cnt - q * kHeavyChunk;
+          heavy.e[at + q] = h;
         }
-        const uint32_t nch = (cnt + kHeavyChunk - 1) / kHeavyChunk;
-        const uint64_t at = ok ? atomicAdd((unsigned long long*)heavy.n, (unsigned long long)nch) : 0;
-        ok &= at + nch <= heavy.cap;
-        if (ok) {
-          for (uint32_t q = 0; q < nch; ++q) {
-            HeavyChunk h;
-            h.prow = row;
-            h.out0 = out0 + (uint64_t)q * kHeavyChunk;
-            h.brow = st + q * kHeavyChunk;
-            h.len = q + 1 < nch ? kHeavyChunk : cnt - q * kHeavyChunk;
-            heavy.e[at + q] = h;
-          }
-        } else {
-          atomicOr(overflow, 1u);
-        }
+      } else {
+        atomicOr(overflow, 1u);
       }
-      if (hv) cnt = 0;
+      cnt = 0;
     }
-    uint64_t inc = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t v = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= (uint32_t)o) inc += v;
-    }
-    const uint64_t excl = inc - cnt;
-    const uint64_t wtot = __shfl_sync(0xffffffffu, inc, 31);
-    if (wtot == 0) continue;
-    if (lane == 0) atomicAdd(total, (unsigned long long)wtot);
-    uint64_t base = 0;
-    if (!FILTER) {
-      if (lane == 0) base = atomicAdd(cursor, (unsigned long long)wtot);
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (base + wtot > cap) {
-        if (lane == 0) atomicOr(overflow, 1u);
-        continue;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_sum<kDirT, uint32_t>(cnt, red, &tot);
+    s_off[threadIdx.x] = ex;
+    s_start[threadIdx.x] = st;
+    if (threadIdx.x == 0 && tot) {
+      atomicAdd(total, (unsigned long long)tot);
+      if (!FILTER) {
+        s_base = atomicAdd(cursor, (unsigned long long)tot);
+        if (s_base + tot > cap) atomicOr(overflow, 1u);
       }
     }
-    for (uint64_t ob = 0; ob < wtot; ob += 32) {
-      const uint64_t o = ob + lane;
-      const bool valid = o < wtot;
-      // the last lane whose range starts at or before o holds output o
-      uint32_t r = 0;
-#pragma unroll
-      for (uint32_t step = 16; step > 0; step >>= 1) {
-        const uint64_t e = __shfl_sync(0xffffffffu, excl, (r + step) & 31u);
-        if (r + step < 32 && e <= o) r += step;
-      }
-      const uint64_t er = __shfl_sync(0xffffffffu, excl, r);
-      const uint32_t sr = __shfl_sync(0xffffffffu, st, r);
-      const uint64_t prow = w * 32 + r;
-      const uint64_t brow = (uint64_t)sr + (o - er);
+    __syncthreads();
+    if (tot == 0) continue;  // uniform: nothing of this block reads s_off
+    for (uint32_t ob = 0; ob < tot; ob += kDirT) {
+      const uint32_t o = ob + threadIdx.x;
+      const bool valid = o < tot;
       uint32_t vals[kMaxK] = {0, 0, 0, 0};
       bool keep = valid;
       if (valid) {
+        uint32_t lo = 0, hi = kDirT;  // the last row whose range starts at or before o
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (s_off[mid] <= o)
+            lo = mid;
+          else
+            hi = mid;
+        }
+        const uint64_t prow = b0 + lo;
+        const uint64_t brow = (uint64_t)s_start[lo] + (o - s_off[lo]);
 #pragma unroll
         for (int k = 0; k < kMaxK; ++k)
           if (k < (int)j.out_k) vals[k] = ref_value(j, j.probe, j.out[k], prow, brow);
@@ -396,15 +386,18 @@ __global__ void __launch_bounds__(kDirT) k_join_direct(const JoinSpec j, ColsOut
         }
       }
       uint64_t pos;
-      if (FILTER) {
-        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-        uint64_t cb = 0;
-        if (lane == 0 && bal) cb = atomicAdd(cursor, (unsigned long long)__popc(bal));
-        cb = __shfl_sync(0xffffffffu, cb, 0);
-        pos = cb + __popc(bal & lt);
-        if (bal && cb + __popc(bal) > cap && lane == 0) atomicOr(overflow, 1u);
+      if (FILTER) {  // survivors packed with one claim per 256 outputs
+        uint32_t n_keep;
+        const uint32_t local = block_exclusive_sum<kDirT, uint32_t>(keep ? 1u : 0u, red, &n_keep);
+        if (threadIdx.x == 0) {
+          s_base = n_keep ? atomicAdd(cursor, (unsigned long long)n_keep) : 0ull;
+          if (n_keep && s_base + n_keep > cap) atomicOr(overflow, 1u);
+        }
+        __syncthreads();
+        pos = s_base + local;
+        __syncthreads();
       } else {
-        pos = base + o;
+        pos = s_base + o;
       }
       if (keep && pos < cap) {
 #pragma unroll
@@ -412,6 +405,7 @@ __global__ void __launch_bounds__(kDirT) k_join_direct(const JoinSpec j, ColsOut
           if (k < (int)j.out_k) out.c[k][pos] = vals[k];
       }
     }
+    __syncthreads();  // s_off, s_start and s_base are rewritten by the next rows
   }
 }
 
@@ -435,7 +429,7 @@ cudaError_t join_direct(Ctx& c, const JoinSpec& j, ColsOut out, uint64_t* d_curs
                         const HeavyList& heavy) {
   if (j.n_probe == 0) return cudaSuccess;
   uint64_t blocks = (j.n_probe + kDirT - 1) / kDirT;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > 152 * 8) blocks = 152 * 8;
   const bool filter = j.n_neq > 0 || j.n_eq > 0;
   ProfScope p(c, kJoinDirect, (4.0 + 16.0 + 4.0 * j.out_k) * j.n_probe);
   auto* cur = reinterpret_cast<unsigned long long*>(d_cursor);

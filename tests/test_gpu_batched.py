@@ -56,7 +56,7 @@ def test_batched_with_estimator_is_exact(cdl, oracle_lib):
     with cdl.Engine() as t:
         t.estimator_train(X, y, epochs=1500)
         params = t.estimator_params()
-    with cdl.Engine(n_instances=10, estimator=1, est_params=params) as e:
+    with cdl.Engine(n_instances=10, estimator=1, est_params=params, est_min_rows=1) as e:
         e.load_program(prog)
         st = e.run()
         got = e.export("tc_path")

@@ -117,7 +117,7 @@ def test_predicted_joins_are_exact_and_cheaper(cdl, oracle_lib, trained, make):
     prog = make()
     want = oracle_lib.run_program(prog)
     exact, st0 = cdl.run_program(prog)
-    with cdl.Engine(estimator=1, est_params=params) as e:
+    with cdl.Engine(estimator=1, est_params=params, est_min_rows=1) as e:
         e.load_program(prog)
         st = e.run()
         got = {nm: e.export(nm) for nm in prog.arity}
@@ -134,7 +134,7 @@ def test_forced_underprediction_falls_back_exactly(cdl, oracle_lib, trained):
     _, _, params, _ = trained
     prog = W.sg_program(W.random_forest(5000, 11))
     want = oracle_lib.run_program(prog)
-    with cdl.Engine(estimator=1, est_params=params, est_margin=-40.0) as e:
+    with cdl.Engine(estimator=1, est_params=params, est_margin=-40.0, est_min_rows=1) as e:
         e.load_program(prog)
         st = e.run()
         got = e.export("sg")
@@ -144,7 +144,7 @@ def test_forced_underprediction_falls_back_exactly(cdl, oracle_lib, trained):
 
 def test_estimator_without_weights_is_exact(cdl, oracle_lib):
     prog = W.tc_program(W.er_graph(200, 300, 3))
-    with cdl.Engine(estimator=1) as e:
+    with cdl.Engine(estimator=1, est_min_rows=1) as e:
         e.load_program(prog)
         st = e.run()
         got = e.export("path")
@@ -183,7 +183,7 @@ def hot_key_program(with_filter):
 def test_hot_keys_through_the_single_pass_join(cdl, oracle_lib, with_filter):
     prog = hot_key_program(with_filter)
     want = oracle_lib.run_program(prog)
-    with cdl.Engine(estimator=1, est_params=constant_network(20.0)) as e:
+    with cdl.Engine(estimator=1, est_params=constant_network(20.0), est_min_rows=1) as e:
         e.load_program(prog)
         st = e.run()
         got = e.export("out")
