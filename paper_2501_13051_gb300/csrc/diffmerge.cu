@@ -268,7 +268,7 @@ __device__ __forceinline__ uint32_t pad(uint32_t i) { return i + (i >> 5); }
 constexpr int kShiftWords = kDTile + 1 + (kDTile + 1) / 32 + 1;
 
 template <int K>
-__global__ void __launch_bounds__(kDT) k_merge_write(ColsIn F, uint64_t nF, ColsIn U, uint64_t nU,
+__global__ void __launch_bounds__(kDT, 5) k_merge_write(ColsIn F, uint64_t nF, ColsIn U, uint64_t nU,
                                                      const uint64_t* __restrict__ splits,
                                                      const uint32_t* __restrict__ corank,
                                                      const uint64_t* __restrict__ tile_pre,
