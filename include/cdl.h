@@ -199,6 +199,20 @@ cdl_status cdl_relation_size(cdl_engine* e, cdl_rel rel, uint64_t* n);
 cdl_status cdl_relation_export(cdl_engine* e, cdl_rel rel, uint32_t* const* cols, uint64_t cap,
                                uint64_t* n_written, int on_device);
 
+/* Copies rows [first, first + count) of rel (sorted and unique, as
+ * cdl_relation_export orders them) into cols[k] (count tuples each; host
+ * memory if on_device == 0).  A range past the size gives CDL_E_CAPACITY
+ * and writes nothing. */
+cdl_status cdl_relation_export_rows(cdl_engine* e, cdl_rel rel, uint64_t first, uint64_t count,
+                                    uint32_t* const* cols, int on_device);
+
+/* Batched runs (options.n_instances > 0): the tuples of instance `instance`
+ * are rows [*first, *first + *count) of rel, column 0 holding the instance
+ * id.  CDL_E_INVALID for an unbatched engine or an instance id >=
+ * n_instances. */
+cdl_status cdl_instance_rows(cdl_engine* e, cdl_rel rel, uint32_t instance, uint64_t* first,
+                             uint64_t* count);
+
 /* Per-kernel timing gathered while options.timing != 0: for kernel class
  * idx (0..), its name, launches, summed device milliseconds and summed
  * algorithmic bytes.  CDL_E_INVALID when idx is past the last class. */

@@ -111,6 +111,8 @@ def lib():
         "cdl_run": (ctypes.c_int, [VP, P(Stats)]),
         "cdl_relation_size": (ctypes.c_int, [VP, U32, P(U64)]),
         "cdl_relation_export": (ctypes.c_int, [VP, U32, PP, U64, P(U64), ctypes.c_int]),
+        "cdl_relation_export_rows": (ctypes.c_int, [VP, U32, U64, U64, PP, ctypes.c_int]),
+        "cdl_instance_rows": (ctypes.c_int, [VP, U32, U32, P(U64), P(U64)]),
         "cdl_kernel_profile": (ctypes.c_int, [VP, U32, ctypes.c_char_p, ctypes.c_size_t, P(U64),
                                               P(ctypes.c_double), P(ctypes.c_double)]),
         "cdl_last_error": (ctypes.c_char_p, [VP]),
@@ -409,6 +411,23 @@ class Engine:
         n = ctypes.c_uint64()
         self._check(self._L.cdl_relation_size(self._h, self.rels[name], ctypes.byref(n)))
         return n.value
+
+    def instance_rows(self, name: str, instance: int):
+        """Batched runs: (first, count) of the instance's rows in the sorted relation."""
+        f, c = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self._L.cdl_instance_rows(self._h, self.rels[name], instance, ctypes.byref(f),
+                                              ctypes.byref(c)))
+        return f.value, c.value
+
+    def export_instance(self, name: str, instance: int):
+        """Batched runs: the instance's tuples, instance column included, as an
+        (n, arity) numpy array."""
+        ar = self.arity[name]
+        first, n = self.instance_rows(name, instance)
+        res = np.zeros((ar, max(n, 1)), dtype=np.uint32)
+        ptrs = _ptrs([res[k].ctypes.data for k in range(ar)])
+        self._check(self._L.cdl_relation_export_rows(self._h, self.rels[name], first, n, ptrs, 0))
+        return np.ascontiguousarray(res[:, :n].T)
 
     def export(self, name: str, device: bool = False, out=None):
         """Sorted unique tuples: (n, arity) numpy array, or with device=True a

@@ -2207,6 +2207,47 @@ cdl_status cdl_relation_export(cdl_engine* e, cdl_rel rel, uint32_t* const* cols
   return er == cudaSuccess ? CDL_OK : e->cuda_fail(er, "export");
 }
 
+cdl_status cdl_relation_export_rows(cdl_engine* e, cdl_rel rel, uint64_t first, uint64_t count,
+                                    uint32_t* const* cols, int on_device) {
+  if (!e) return CDL_E_INVALID;
+  if (rel >= e->rels.size()) return e->fail(CDL_E_INVALID, "no such relation");
+  const Relation& R = *e->rels[rel];
+  if (first > R.full.n || count > R.full.n - first)
+    return e->fail(CDL_E_CAPACITY, "row range past the relation");
+  if (count == 0) return CDL_OK;
+  if (!cols) return CDL_E_INVALID;
+  cudaError_t er = cudaSuccess;
+  for (uint32_t k = 0; k < R.arity && er == cudaSuccess; ++k) {
+    if (!cols[k]) return e->fail(CDL_E_INVALID, "null column pointer");
+    er = cudaMemcpyAsync(cols[k], R.full.c[k] + first, count * 4,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, e->st);
+  }
+  if (er == cudaSuccess) er = cudaStreamSynchronize(e->st);
+  return er == cudaSuccess ? CDL_OK : e->cuda_fail(er, "export rows");
+}
+
+cdl_status cdl_instance_rows(cdl_engine* e, cdl_rel rel, uint32_t instance, uint64_t* first,
+                             uint64_t* count) {
+  if (!e || !first || !count) return CDL_E_INVALID;
+  if (rel >= e->rels.size()) return e->fail(CDL_E_INVALID, "no such relation");
+  if (!e->opt.n_instances || instance >= e->opt.n_instances)
+    return e->fail(CDL_E_INVALID, "no such instance");
+  const Relation& R = *e->rels[rel];
+  *first = *count = 0;
+  if (R.full.n == 0) return CDL_OK;
+  DBuf b = e->alloc(8 * (e->opt.n_instances + 1));
+  if (!b.p) return e->fail(CDL_E_NOMEM, "instance bounds");
+  uint64_t* d = static_cast<uint64_t*>(b.p);
+  uint64_t h[2] = {0, 0};
+  cudaError_t er = instance_bounds(e->ctx, R.full.c[0], R.full.n, e->opt.n_instances, d);
+  if (er == cudaSuccess) er = cudaMemcpyAsync(h, d + instance, 16, cudaMemcpyDeviceToHost, e->st);
+  if (er == cudaSuccess) er = cudaStreamSynchronize(e->st);
+  if (er != cudaSuccess) return e->cuda_fail(er, "instance bounds");
+  *first = h[0];
+  *count = h[1] - h[0];
+  return CDL_OK;
+}
+
 cdl_status cdl_kernel_profile(cdl_engine* e, uint32_t idx, char* name, size_t name_cap,
                               uint64_t* launches, double* ms, double* bytes) {
   if (!e) return CDL_E_INVALID;

@@ -47,3 +47,29 @@ def test_structs_match_header_sizes():
     assert ctypes.sizeof(cdl.ColRef) == 8
     assert ctypes.sizeof(cdl.Atom) == 16
     assert ctypes.sizeof(cdl.Stats) == 8 * 14
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/cdl.h compiles as C99 (no C++ types in the boundary) and its
+    declarations are usable from C."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_cdl.c"
+    src.write_text(
+        '#include "cdl.h"\n'
+        "int main(void) {\n"
+        "  cdl_options o;\n"
+        "  cdl_options_default(&o);\n"
+        "  cdl_engine* e = 0;\n"
+        "  cdl_stats st = {0};\n"
+        "  (void)st;\n"
+        "  return cdl_create(&o, &e) == CDL_OK ? 0 : 1;\n"
+        "}\n")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

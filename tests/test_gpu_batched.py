@@ -46,6 +46,20 @@ def test_batched_equals_each_instance(cdl, oracle_lib, count, seed, lo, hi, reti
     assert max(st.iters_per_instance) == st.iterations
 
 
+def test_export_of_one_instance(cdl):
+    graphs, kinds = W.batched_instances(9, 83, 50, 2000)
+    prog = W.batched_program(graphs, kinds)
+    with cdl.Engine(n_instances=9) as e:
+        e.load_program(prog)
+        e.run()
+        rows = e.export("tc_path")
+        for i in range(9):
+            mine = e.export_instance("tc_path", i)
+            assert np.array_equal(mine, rows[rows[:, 0] == i]), i
+        with pytest.raises(cdl.CdlError):
+            e.instance_rows("tc_path", 9)
+
+
 def test_batched_with_estimator_is_exact(cdl, oracle_lib):
     graphs, kinds = W.batched_instances(10, 79, 100, 4000)
     prog = W.batched_program(graphs, kinds)
