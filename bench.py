@@ -160,6 +160,19 @@ def describe_sample(spec, derived, secs):
     return f"{what}, seed {spec['seed']}: {derived} tuples in {secs:.2f} s"
 
 
+def over_ranks(secs, derived, dist, device):
+    """Whole-job (seconds, derived tuples) of N replicas: the slowest rank's
+    time and every rank's tuples (one rank: unchanged)."""
+    if dist is None:
+        return secs, derived
+    import torch
+    t = torch.tensor([secs, float(derived)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(mx[0]), int(t[1])
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -378,12 +391,7 @@ def bench_gb300(args, rank, world, dist):
     barrier()
     clocks = clk.stop()
     secs = ev0.elapsed_time(ev1) * 1e-3
-    if dist is not None:
-        t = torch.tensor([secs, float(derived)], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        secs, derived = float(mx[0]), int(t[1])
+    secs, derived = over_ranks(secs, derived, dist, "cuda")
     value = derived / secs
     per_step = st.derived_tuples
 
@@ -439,8 +447,8 @@ def bench_gb300(args, rank, world, dist):
     e1.record()
     torch.cuda.synchronize()
     barrier()
-    secs_e2e = e0.elapsed_time(e1) * 1e-3
-    e2e = {"value": d_e2e * world / secs_e2e, "unit": "tuples/s",
+    secs_e2e, d_e2e = over_ranks(e0.elapsed_time(e1) * 1e-3, d_e2e, dist, "cuda")
+    e2e = {"value": d_e2e / secs_e2e, "unit": "tuples/s",
            "h2d_bytes_per_step": int(sum(4 * c.size for cols in host_cols.values() for c in cols)),
            "d2h_bytes_per_step": int(sum(4 * sizes[nm] * prog.arity[nm] for nm in idb))}
 
