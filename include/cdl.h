@@ -56,7 +56,8 @@ typedef enum {
   CDL_E_CAPACITY = -3, /* an output buffer or a 2^32 size limit is too small */
   CDL_E_VALUE = -4,    /* input holds the reserved value 0xFFFFFFFF */
   CDL_E_MAXITER = -5,  /* the fixpoint needs more rounds than max_iters */
-  CDL_E_TIMEOUT = -6,  /* a bounded device-side wait ran out */
+  CDL_E_TIMEOUT = -6,  /* a bounded device-side wait ran out (no kernel of this library
+                          waits on another block; the code stays reserved) */
   CDL_E_CUDA = -7,     /* a CUDA runtime call failed */
   CDL_E_STATE = -8     /* call not valid in the engine's current state */
 } cdl_status;
@@ -80,7 +81,8 @@ typedef struct {
   void* stream;        /* cudaStream_t every kernel of the engine runs on */
   uint64_t mem_limit;  /* bytes of device memory the engine may hold; 0 = no limit */
   uint64_t max_iters;  /* rounds that may produce new tuples; 0 = no limit */
-  uint64_t spin_limit; /* iterations of any device-side wait; 0 = default (2^26) */
+  uint64_t spin_limit; /* bound of any device-side wait; 0 = default (2^26).  No kernel of
+                          this library spins on another block, so nothing reads it now */
   uint32_t timing;     /* CUDA-event timing of kernel launches: 0 off; 1 every kernel
                           class; any other value is a mask, bit (1 + c) timing class c
                           (the classes cdl_kernel_profile lists), so that events wrap

@@ -131,65 +131,6 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* smem, T* total) {
   return res;
 }
 
-// ------------------------------------------------------------------------
-// Decoupled look-back (Merrill & Garland, "Single-pass parallel prefix scan
-// with decoupled look-back", NVIDIA tech report NVR-2016-002).  status[t]
-// holds a flag in its top two bits (0 nothing yet, AGG: the tile's own
-// count, INC: the count of tiles 0..t) and the value in the low 62 bits;
-// the array starts zeroed and tiles are numbered in the order their blocks
-// start, so every tile waited on belongs to a running or finished block.
-constexpr uint64_t kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62, kValMask = (1ull << 62) - 1;
-
-__device__ __forceinline__ uint64_t ld_volatile(const uint64_t* p) {
-  return *reinterpret_cast<const volatile uint64_t*>(p);
-}
-__device__ __forceinline__ void st_volatile(uint64_t* p, uint64_t v) {
-  *reinterpret_cast<volatile uint64_t*>(p) = v;
-}
-
-// Called by all 32 lanes of one warp: publishes tile's aggregate, sums the
-// tiles before it 32 at a time (aggregates up to the nearest inclusive
-// prefix), publishes tile's inclusive prefix and returns the exclusive one
-// to every lane.  A window still missing a value is polled at most
-// spin_limit times; then kErrTimeout is raised and the sum so far is used,
-// which can only be smaller than the true prefix.
-__device__ __forceinline__ uint64_t warp_look_back(uint64_t* status, uint64_t tile, uint64_t agg,
-                                                   uint64_t spin_limit, uint32_t* err) {
-  const uint32_t lane = threadIdx.x & 31u;
-  if (tile == 0) {
-    if (lane == 0) st_volatile(status, kFlagInc | agg);
-    return 0;
-  }
-  if (lane == 0) st_volatile(status + tile, kFlagAgg | agg);
-  uint64_t prefix = 0, spins = 0;
-  int64_t end = (int64_t)tile;  // window: tiles [end - 32, end)
-  while (end > 0) {
-    const int64_t idx = end - 1 - (int64_t)lane;  // lane 0 = nearest predecessor
-    const uint64_t v = idx >= 0 ? ld_volatile(status + idx) : kFlagInc;
-    const uint64_t flag = v & ~kValMask;
-    const uint32_t inc = __ballot_sync(0xffffffffu, flag == kFlagInc);
-    const uint32_t empty = __ballot_sync(0xffffffffu, flag == 0);
-    const uint32_t stop = inc ? (uint32_t)(__ffs(inc) - 1) : 32u;  // nearest inclusive prefix
-    const uint32_t need = stop < 31u ? ((2u << stop) - 1u) : 0xffffffffu;
-    if (empty & need) {
-      if (++spins > spin_limit) {
-        if (lane == 0 && err) atomicOr(err, kErrTimeout);
-        break;
-      }
-      __nanosleep(32);
-      continue;
-    }
-    uint64_t x = lane <= stop ? (v & kValMask) : 0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    prefix += x;
-    if (stop < 32u) break;
-    end -= 32;
-  }
-  if (lane == 0) st_volatile(status + tile, kFlagInc | (prefix + agg));
-  return prefix;
-}
-
 // Device-sized launches (a round captured in a CUDA graph): the grid is
 // sized for a capacity known to the host, the actual size is read from
 // device memory and clamped to that capacity, so no access can leave the
