@@ -68,3 +68,11 @@ def test_missing_cache_file_is_not_an_error(cdl, oracle_lib, tmp_path):
     prog = W.tc_program(W.er_graph(300, 450, 5))
     got, st = cdl.run_program(prog, autotune=1, tune_cache=str(tmp_path / "absent.txt"))
     assert np.array_equal(got["path"], oracle_lib.run_program(prog).relations["path"])
+
+
+def test_unwritable_cache_file_is_reported(cdl, tmp_path):
+    prog = W.tc_program(W.er_graph(1000, 1500, 6))  # sorts large enough to be timed
+    bad = str(tmp_path / "no-such-dir" / "tune.txt")
+    with pytest.raises(cdl.CdlError) as ex:
+        cdl.run_program(prog, autotune=2, tune_cache=bad)
+    assert ex.value.name == "CDL_E_INVALID"
