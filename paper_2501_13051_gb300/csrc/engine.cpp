@@ -317,7 +317,6 @@ constexpr uint32_t kSlotErr = 0, kSlotScratch = 1, kSlotAux = 2, kSlotDirTotal =
                    kSlotDelta = 8 + kMaxRels,
                    kCtlSlots = 8 + 2 * kMaxRels;
 constexpr int kEstFloats = 32;  // 16 features, the prediction, padding
-constexpr int Engine_kX = 4;    // export side streams
 
 }  // namespace
 
@@ -483,23 +482,7 @@ struct cdl_engine {
     return install_weights(nullptr);
   }
 
-  // side streams of exports to pinned host memory (created on first use)
-  cudaStream_t xst[Engine_kX] = {};
-  cudaEvent_t xev[Engine_kX + 1] = {};
-  bool export_streams() {
-    if (xst[0]) return true;
-    for (int i = 0; i < Engine_kX; ++i)
-      if (cudaStreamCreateWithFlags(&xst[i], cudaStreamNonBlocking) != cudaSuccess) return false;
-    for (int i = 0; i <= Engine_kX; ++i)
-      if (cudaEventCreateWithFlags(&xev[i], cudaEventDisableTiming) != cudaSuccess) return false;
-    return true;
-  }
-
   ~cdl_engine() {
-    for (int i = 0; i < Engine_kX; ++i)
-      if (xst[i]) cudaStreamDestroy(xst[i]);
-    for (int i = 0; i <= Engine_kX; ++i)
-      if (xev[i]) cudaEventDestroy(xev[i]);
     cache.clear();
     rels.clear();
     ctl.reset();
@@ -2170,38 +2153,11 @@ cdl_status cdl_relation_export(cdl_engine* e, cdl_rel rel, uint32_t* const* cols
   if (cap < R.full.n) return e->fail(CDL_E_CAPACITY, "export buffer too small");
   if (R.full.n == 0) return CDL_OK;
   if (!cols) return CDL_E_INVALID;
-  for (uint32_t k = 0; k < R.arity; ++k)
-    if (!cols[k]) return e->fail(CDL_E_INVALID, "null column pointer");
-  // to pinned host memory: 64 MB chunks spread over several streams, so
-  // that several copy engines drive the host link at once
-  bool pinned = !on_device && R.full.n * 4ull * R.arity > (64ull << 20);
-  for (uint32_t k = 0; k < R.arity && pinned; ++k) {
-    cudaPointerAttributes at{};
-    pinned = cudaPointerGetAttributes(&at, cols[k]) == cudaSuccess && at.type == cudaMemoryTypeHost;
-  }
-  cudaGetLastError();
   cudaError_t er = cudaSuccess;
-  if (pinned && e->export_streams()) {
-    er = cudaEventRecord(e->xev[Engine_kX], e->st);
-    for (int i = 0; i < Engine_kX && er == cudaSuccess; ++i)
-      er = cudaStreamWaitEvent(e->xst[i], e->xev[Engine_kX], 0);
-    const uint64_t chunk = (64ull << 20) / 4;  // rows
-    int next = 0;
-    for (uint32_t k = 0; k < R.arity && er == cudaSuccess; ++k)
-      for (uint64_t r0 = 0; r0 < R.full.n && er == cudaSuccess; r0 += chunk) {
-        const uint64_t rows = std::min(chunk, R.full.n - r0);
-        er = cudaMemcpyAsync(cols[k] + r0, R.full.c[k] + r0, rows * 4, cudaMemcpyDeviceToHost,
-                             e->xst[next]);
-        next = (next + 1) % Engine_kX;
-      }
-    for (int i = 0; i < Engine_kX && er == cudaSuccess; ++i) {
-      er = cudaEventRecord(e->xev[i], e->xst[i]);
-      if (er == cudaSuccess) er = cudaStreamWaitEvent(e->st, e->xev[i], 0);
-    }
-  } else {
-    for (uint32_t k = 0; k < R.arity && er == cudaSuccess; ++k)
-      er = cudaMemcpyAsync(cols[k], R.full.c[k], R.full.n * 4,
-                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, e->st);
+  for (uint32_t k = 0; k < R.arity && er == cudaSuccess; ++k) {
+    if (!cols[k]) return e->fail(CDL_E_INVALID, "null column pointer");
+    er = cudaMemcpyAsync(cols[k], R.full.c[k], R.full.n * 4,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, e->st);
   }
   if (er == cudaSuccess) er = cudaStreamSynchronize(e->st);
   return er == cudaSuccess ? CDL_OK : e->cuda_fail(er, "export");

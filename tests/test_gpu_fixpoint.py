@@ -134,9 +134,8 @@ def test_export_capacity(cdl):
         assert st == -3 and got.value == 10
 
 
-def test_export_to_pinned_memory_in_chunks(cdl):
-    # > 64 MB of columns: the export to pinned host memory is split into
-    # chunks over several streams; it must equal the pageable export
+def test_export_to_pinned_memory(cdl):
+    # > 64 MB of columns into pinned host buffers: equal to the pageable export
     import torch
     prog = W.sg_program(W.random_forest(20000, 41))
     with cdl.Engine() as e:
