@@ -395,7 +395,7 @@ def bench_gb300(args, rank, world, dist):
     value = derived / secs
     per_step = st.derived_tuples
 
-    # ---- the plain exact form (no estimator, no tuner), timed the same way
+    # ---- the plain exact form (no estimator, no tuner, no graph), timed the same way
     plain = None
     if form:
         torch.cuda.synchronize()
@@ -405,7 +405,8 @@ def bench_gb300(args, rank, world, dist):
         for i in range(args.steps):
             if i:
                 flush.fill_(i & 0xFF)
-            pd += step(False, plain=True)[0].derived_tuples
+            # the same events as the form's timed steps (last step only)
+            pd += step([dominant] if i == args.steps - 1 else False, plain=True)[0].derived_tuples
         p1.record()
         torch.cuda.synchronize()
         psecs = p0.elapsed_time(p1) * 1e-3
