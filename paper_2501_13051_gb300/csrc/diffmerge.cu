@@ -399,13 +399,17 @@ cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, u
     k_dm_tiles<<<1, 32, 0, c.st>>>(dm, n_full, n_fresh, d_tiles);
   }
   const size_t smem_count = sizeof(uint32_t) * K * kDTile;
-  static int resident = 0;  // blocks of k_count_new<K> the whole GPU holds at once
-  cudaError_t e = cudaSuccess;
+  // blocks of k_count_new<K> a whole GPU holds at once, per device
+  constexpr int kDevices = 64;
+  static int resident_of[kDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int& resident = resident_of[dev < kDevices ? dev : 0];
   if (!resident) {
     e = cudaFuncSetAttribute(k_count_new<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_count);
-    int per_sm = 0, dev = 0, sms = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    int per_sm = 0, sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_new<K>, kDT, smem_count);

@@ -73,3 +73,17 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_no_silent_fallback(monkeypatch, tmp_path):
+    """The product path fails loudly: without the built library, and without
+    a GPU (as in this container), nothing runs on the CPU instead."""
+    monkeypatch.setattr(cdl, "_lib", None)
+    monkeypatch.setattr(cdl, "LIB_PATH", str(tmp_path / "libcdl.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        cdl.lib()
+    monkeypatch.undo()
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(Exception):
+            cdl.Engine()
