@@ -201,6 +201,18 @@ cdl_status cdl_relation_size(cdl_engine* e, cdl_rel rel, uint64_t* n);
 cdl_status cdl_relation_export(cdl_engine* e, cdl_rel rel, uint32_t* const* cols, uint64_t cap,
                                uint64_t* n_written, int on_device);
 
+/* Checkpoints (not in the paper).  cdl_checkpoint_save, after cdl_run
+ * returned CDL_OK or CDL_E_MAXITER, writes every relation's full and delta
+ * versions and the rounds completed (with their delta sizes) to a file.
+ * cdl_checkpoint_load, on a fresh engine whose relations and rules are
+ * declared as before and before cdl_run, restores them: cdl_run then
+ * continues the semi-naive loop from the saved round with the saved deltas
+ * (iterations, rounds and per-round sizes continue the saved ones).
+ * CDL_E_STATE out of order, CDL_E_INVALID for an unreadable, foreign or
+ * mismatching file and for batched engines. */
+cdl_status cdl_checkpoint_save(cdl_engine* e, const char* path);
+cdl_status cdl_checkpoint_load(cdl_engine* e, const char* path);
+
 /* Copies rows [first, first + count) of rel (sorted and unique, as
  * cdl_relation_export orders them) into cols[k] (count tuples each; host
  * memory if on_device == 0).  A range past the size gives CDL_E_CAPACITY

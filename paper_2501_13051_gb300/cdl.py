@@ -112,6 +112,8 @@ def lib():
         "cdl_relation_size": (ctypes.c_int, [VP, U32, P(U64)]),
         "cdl_relation_export": (ctypes.c_int, [VP, U32, PP, U64, P(U64), ctypes.c_int]),
         "cdl_relation_export_rows": (ctypes.c_int, [VP, U32, U64, U64, PP, ctypes.c_int]),
+        "cdl_checkpoint_save": (ctypes.c_int, [VP, ctypes.c_char_p]),
+        "cdl_checkpoint_load": (ctypes.c_int, [VP, ctypes.c_char_p]),
         "cdl_instance_rows": (ctypes.c_int, [VP, U32, U32, P(U64), P(U64)]),
         "cdl_kernel_profile": (ctypes.c_int, [VP, U32, ctypes.c_char_p, ctypes.c_size_t, P(U64),
                                               P(ctypes.c_double), P(ctypes.c_double)]),
@@ -411,6 +413,14 @@ class Engine:
         n = ctypes.c_uint64()
         self._check(self._L.cdl_relation_size(self._h, self.rels[name], ctypes.byref(n)))
         return n.value
+
+    def checkpoint_save(self, path: str) -> None:
+        """Writes every relation's full and delta versions and the rounds done."""
+        self._check(self._L.cdl_checkpoint_save(self._h, os.fsencode(path)))
+
+    def checkpoint_load(self, path: str) -> None:
+        """Restores a checkpoint before run(): the run continues from it."""
+        self._check(self._L.cdl_checkpoint_load(self._h, os.fsencode(path)))
 
     def instance_rows(self, name: str, instance: int):
         """Batched runs: (first, count) of the instance's rows in the sorted relation."""

@@ -399,6 +399,12 @@ struct cdl_engine {
   cudaGraphExec_t gexec = nullptr;
   uint64_t glaunches_per_round = 0;
   uint64_t g_rounds = 0, g_builds = 0;
+  // checkpoints: the rounds a loaded checkpoint had completed, and the
+  // rounds of the last cdl_run (what a checkpoint saves)
+  uint64_t resume_rounds = 0, resume_iters = 0;
+  std::vector<uint64_t> resume_per_round;
+  uint64_t last_rounds = 0, last_iters = 0;
+  std::vector<uint64_t> last_per_round;
   static constexpr uint64_t kGraphRounds = 1 << 16;  // per-round sizes the device records
   DBuf inst_last;  // batched runs: last round each instance derived a tuple
   std::vector<uint64_t> h_inst;
@@ -1817,8 +1823,9 @@ struct cdl_engine {
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
     cudaEventRecord(t0, st);
-    uint64_t iterations = 0, rounds = 0;
-    std::vector<uint64_t> per_round;
+    uint64_t iterations = resume_iters, rounds = resume_rounds;
+    std::vector<uint64_t> per_round = resume_per_round;
+    const uint64_t first_semi = std::max<uint64_t>(2, resume_rounds + 1);
     cdl_status status = CDL_OK;
     const uint32_t nr = (uint32_t)rels.size();
     est_pred = est_over = 0;
@@ -1850,10 +1857,10 @@ struct cdl_engine {
     grec.clear();
     grec_bad = graph_ready = false;
     g_rounds = g_builds = 0;
-    for (uint64_t round = 1; status == CDL_OK; ++round) {
+    for (uint64_t round = resume_rounds + 1; status == CDL_OK; ++round) {
       cur_round = round;
       cudaError_t e = cudaSuccess;
-      recording = opt.graph && round == 2;  // the first semi-naive round is the plan
+      recording = opt.graph && round == first_semi;  // the first semi-naive round is the plan
       status = eval_round(round);
       recording = false;
       if (status != CDL_OK) break;
@@ -1917,11 +1924,11 @@ struct cdl_engine {
         status = fail(CDL_E_MAXITER, "the fixpoint needs more rounds than max_iters");
         break;
       }
-      if (opt.graph && round == 2) {
+      if (opt.graph && round == first_semi) {
         graph_ready = graph_plan();
         if (graph_ready) graph_caps();
       }
-      if (graph_ready && round >= 2) {  // the next rounds on the device
+      if (graph_ready && round >= first_semi) {  // the next rounds on the device
         bool finished = false;
         status = graph_run(round, per_round, iterations, finished);
         rounds = round;
@@ -1930,6 +1937,9 @@ struct cdl_engine {
     }
     graph_release();
     if (opt.n_instances && status == CDL_OK) status = assemble();
+    last_rounds = rounds;
+    last_iters = iterations;
+    last_per_round = per_round;
     tuner.resolve();
     if (tuner.mode == 2 && !tuner.save() && status == CDL_OK)
       status = fail(CDL_E_INVALID, "cannot write the tuner file");
@@ -1970,6 +1980,118 @@ struct cdl_engine {
       }
     }
     return status;
+  }
+
+  // --------------------------------------------------------- checkpoints
+  // File: "CDLCKPT1", rounds, iterations, per-round count and sizes, then per
+  // relation its name, arity, |full|, |delta| and the columns of full and
+  // delta (uint32, host byte order).
+  cdl_status checkpoint_save(const char* path) {
+    if (!ran) return fail(CDL_E_STATE, "nothing to save before cdl_run");
+    if (opt.n_instances) return fail(CDL_E_INVALID, "batched runs are not checkpointed");
+    FILE* f = path ? std::fopen(path, "wb") : nullptr;
+    if (!f) return fail(CDL_E_INVALID, "cannot write the checkpoint file");
+    bool ok = std::fwrite("CDLCKPT1", 1, 8, f) == 8;
+    const uint64_t head[3] = {last_rounds, last_iters, (uint64_t)last_per_round.size()};
+    ok &= std::fwrite(head, 8, 3, f) == 3;
+    ok &= std::fwrite(last_per_round.data(), 8, last_per_round.size(), f) == last_per_round.size();
+    const uint32_t nrel = (uint32_t)rels.size();
+    ok &= std::fwrite(&nrel, 4, 1, f) == 1;
+    std::vector<uint32_t> col;
+    for (auto& rp : rels) {
+      const Relation& R = *rp;
+      const uint32_t nl = (uint32_t)R.name.size();
+      const uint64_t sz[2] = {R.full.n, R.delta.n};
+      ok &= std::fwrite(&nl, 4, 1, f) == 1 && std::fwrite(R.name.data(), 1, nl, f) == nl;
+      ok &= std::fwrite(&R.arity, 4, 1, f) == 1 && std::fwrite(sz, 8, 2, f) == 2;
+      for (const DCols* d : {&R.full, &R.delta})
+        for (uint32_t k = 0; k < R.arity && ok && d->n; ++k) {
+          col.resize(d->n);
+          if (cudaMemcpy(col.data(), d->c[k], 4 * d->n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(f);
+            return fail(CDL_E_CUDA, "checkpoint copy");
+          }
+          ok &= std::fwrite(col.data(), 4, d->n, f) == d->n;
+        }
+    }
+    ok &= std::fclose(f) == 0;
+    return ok ? CDL_OK : fail(CDL_E_INVALID, "checkpoint write failed");
+  }
+
+  cdl_status checkpoint_load(const char* path) {
+    if (ran) return fail(CDL_E_STATE, "checkpoints load before cdl_run");
+    if (opt.n_instances) return fail(CDL_E_INVALID, "batched runs are not checkpointed");
+    FILE* f = path ? std::fopen(path, "rb") : nullptr;
+    if (!f) return fail(CDL_E_INVALID, "cannot read the checkpoint file");
+    auto bad = [&](const char* m) {
+      std::fclose(f);
+      return fail(CDL_E_INVALID, std::string("checkpoint: ") + m);
+    };
+    char magic[8];
+    uint64_t head[3];
+    if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, "CDLCKPT1", 8) != 0)
+      return bad("not a checkpoint");
+    if (std::fread(head, 8, 3, f) != 3 || head[2] > (1ull << 32)) return bad("truncated header");
+    std::vector<uint64_t> pr(head[2]);
+    if (std::fread(pr.data(), 8, pr.size(), f) != pr.size()) return bad("truncated rounds");
+    uint32_t nrel = 0;
+    if (std::fread(&nrel, 4, 1, f) != 1) return bad("truncated header");
+    std::vector<uint32_t> col;
+    for (uint32_t i = 0; i < nrel; ++i) {
+      uint32_t nl = 0, ar = 0;
+      uint64_t sz[2];
+      if (std::fread(&nl, 4, 1, f) != 1 || nl > 4096) return bad("truncated relation");
+      std::string name(nl, '\0');
+      if (std::fread(&name[0], 1, nl, f) != nl || std::fread(&ar, 4, 1, f) != 1 ||
+          std::fread(sz, 8, 2, f) != 2)
+        return bad("truncated relation");
+      auto it = by_name.find(name);
+      if (it == by_name.end() || rels[it->second]->arity != ar)
+        return bad("relation not declared with that arity");
+      Relation& R = *rels[it->second];
+      if (sz[0] > 0xFFFFFFFFull || sz[1] > sz[0]) return bad("bad sizes");
+      DCols* dst[2] = {&R.full, &R.delta};
+      for (int v = 0; v < 2; ++v) {
+        DCols& d = *dst[v];
+        d.clear();
+        if (!alloc_cols(d, ar, std::max<uint64_t>(sz[v], 1))) {
+          std::fclose(f);
+          return fail(CDL_E_NOMEM, "checkpoint buffers");
+        }
+        d.n = sz[v];
+        for (uint32_t k = 0; k < ar && sz[v]; ++k) {
+          col.resize(sz[v]);
+          if (std::fread(col.data(), 4, sz[v], f) != sz[v]) return bad("truncated columns");
+          if (cudaMemcpy(d.c[k], col.data(), 4 * sz[v], cudaMemcpyHostToDevice) != cudaSuccess) {
+            std::fclose(f);
+            return fail(CDL_E_CUDA, "checkpoint copy");
+          }
+        }
+      }
+      if (R.full.n) {  // column bounds, as a load computes them
+        uint32_t* dmax = reinterpret_cast<uint32_t*>(dslot(kSlotScratch + 1));
+        cudaError_t e = check_values(ctx, R.full.in(), ar, R.full.n, dmax);
+        if (e != cudaSuccess) {
+          std::fclose(f);
+          return cuda_fail(e, "checkpoint check");
+        }
+        cdl_status r = fetch(kSlotScratch + 1, 2);
+        if (r != CDL_OK) {
+          std::fclose(f);
+          return r;
+        }
+        const uint32_t* hmax = reinterpret_cast<const uint32_t*>(h_ctl + kSlotScratch + 1);
+        for (uint32_t k = 0; k < ar; ++k) R.bound[k] = std::max(R.bound[k], hmax[k]);
+      }
+      R.version[kFull]++;
+      R.version[kDelta]++;
+    }
+    std::fclose(f);
+    evict_stale();
+    resume_rounds = head[0];
+    resume_iters = head[1];
+    resume_per_round = pr;
+    return CDL_OK;
   }
 
   cdl_status load(uint32_t rel, const uint32_t* const* cols, uint64_t n, int on_device) {
@@ -2161,6 +2283,14 @@ cdl_status cdl_relation_export(cdl_engine* e, cdl_rel rel, uint32_t* const* cols
   }
   if (er == cudaSuccess) er = cudaStreamSynchronize(e->st);
   return er == cudaSuccess ? CDL_OK : e->cuda_fail(er, "export");
+}
+
+cdl_status cdl_checkpoint_save(cdl_engine* e, const char* path) {
+  return e ? e->checkpoint_save(path) : CDL_E_INVALID;
+}
+
+cdl_status cdl_checkpoint_load(cdl_engine* e, const char* path) {
+  return e ? e->checkpoint_load(path) : CDL_E_INVALID;
 }
 
 cdl_status cdl_relation_export_rows(cdl_engine* e, cdl_rel rel, uint64_t first, uint64_t count,

@@ -148,3 +148,61 @@ def test_export_to_pinned_memory(cdl):
         want = e.export("sg")
     got = np.stack([t.numpy().view(np.uint32) for t in pinned], 1)
     assert np.array_equal(got, want)
+
+
+def declare(e, prog):
+    for nm, ar in prog.arity.items():
+        e.relation(nm, ar)
+    for r in prog.rules:
+        e.rule(r.head, r.body, r.neq)
+
+
+@pytest.mark.parametrize("make,stop,graph", [
+    (lambda: W.tc_program(W.er_graph(1000, 1500, 1)), 10, False),
+    (lambda: W.sg_program(W.random_forest(2000, 51)), 4, True),
+    (lambda: W.points_to_program(W.points_to_edb(1 / 2048, 52)), 3, False)])
+def test_checkpoint_and_resume(cdl, oracle_lib, tmp_path, make, stop, graph):
+    prog = make()
+    want = oracle_lib.run_program(prog)
+    path = str(tmp_path / "ckpt.bin")
+    with cdl.Engine(max_iters=stop) as e:
+        e.load_program(prog)
+        with pytest.raises(cdl.CdlError) as ex:
+            e.run()
+        assert ex.value.name == "CDL_E_MAXITER"
+        e.checkpoint_save(path)
+    with cdl.Engine(graph=graph) as e:  # no facts loaded: the checkpoint holds them
+        declare(e, prog)
+        e.checkpoint_load(path)
+        st = e.run()
+        got = {nm: e.export(nm) for nm in prog.arity}
+    for nm in prog.arity:
+        assert np.array_equal(got[nm], want.relations[nm]), nm
+    assert st.iterations == want.iterations and st.rounds == want.rounds
+    per_round = [sum(want.deltas[nm][k] for nm in prog.idb()) for k in range(want.rounds)]
+    assert st.delta_per_round == per_round
+
+
+def test_checkpoint_errors(cdl, tmp_path):
+    prog = W.tc_program(W.er_graph(50, 120, 2))
+    path = str(tmp_path / "ckpt.bin")
+    with cdl.Engine() as e:
+        e.load_program(prog)
+        with pytest.raises(cdl.CdlError) as ex:
+            e.checkpoint_save(path)  # before run
+        assert ex.value.name == "CDL_E_STATE"
+        e.run()
+        e.checkpoint_save(path)
+    junk = tmp_path / "junk.bin"
+    junk.write_bytes(b"not a checkpoint at all")
+    with cdl.Engine() as e:
+        declare(e, prog)
+        with pytest.raises(cdl.CdlError) as ex:
+            e.checkpoint_load(str(junk))
+        assert ex.value.name == "CDL_E_INVALID"
+    with cdl.Engine() as e:  # the same names with another arity
+        e.relation("edge", 3)
+        e.relation("path", 2)
+        with pytest.raises(cdl.CdlError) as ex:
+            e.checkpoint_load(path)
+        assert ex.value.name == "CDL_E_INVALID"
