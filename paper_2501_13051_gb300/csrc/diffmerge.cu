@@ -79,9 +79,12 @@ __device__ __forceinline__ bool resolve(const DevMerge& dm, ColsIn& F, uint64_t&
 
 template <int K>
 __global__ void k_merge_splits(ColsIn F, uint64_t nF, ColsIn U, uint64_t nU,
-                               uint64_t* __restrict__ splits, uint64_t ntiles, DevMerge dm) {
+                               uint64_t* __restrict__ splits, uint64_t ntiles, DevMerge dm,
+                               uint64_t* d_tiles) {
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (!resolve(dm, F, nF, nU, ntiles)) {
+  const bool fits = resolve(dm, F, nF, nU, ntiles);
+  if (d_tiles && t == 0) *d_tiles = fits ? ntiles : 0;  // the scan's length (0: nothing fits)
+  if (!fits) {
     if (t == 0) atomicOr(dm.overflow, 1u);
     return;
   }
@@ -368,13 +371,6 @@ uint64_t dm_tiles(uint64_t n_full, uint64_t n_fresh) {
   return (n_full + n_fresh + kDTile - 1) / kDTile;
 }
 
-// Tiles of a device-sized pair (0 when it does not fit): the scan's length.
-__global__ void k_dm_tiles(DevMerge dm, uint64_t nF, uint64_t nU, uint64_t* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  ColsIn F{};
-  uint64_t ntiles = 0;
-  out[0] = resolve(dm, F, nF, nU, ntiles) ? ntiles : 0;
-}
 
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -393,11 +389,8 @@ cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, u
   uint32_t* corank = reinterpret_cast<uint32_t*>(w);
   w += up256((n_fresh ? n_fresh : 1) * 4);
   void* scan_ws = w;
-  uint64_t* d_tiles = nullptr;  // device-sized: the scan's length, after its workspace
-  if (dm.n_full) {
-    d_tiles = reinterpret_cast<uint64_t*>(w + scan_workspace(tiles));
-    k_dm_tiles<<<1, 32, 0, c.st>>>(dm, n_full, n_fresh, d_tiles);
-  }
+  uint64_t* d_tiles = nullptr;  // device-sized: the scan's length (the split kernel writes it)
+  if (dm.n_full) d_tiles = reinterpret_cast<uint64_t*>(w + scan_workspace(tiles));
   const size_t smem_count = sizeof(uint32_t) * K * kDTile;
   // blocks of k_count_new<K> a whole GPU holds at once, per device
   constexpr int kDevices = 64;
@@ -426,7 +419,7 @@ cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, u
     // New read, co-ranks written; Full sectors are read only where touched
     ProfScope p(c, kDiffCount, (4.0 * K + 4.0) * n_fresh);
     k_merge_splits<K><<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, c.st>>>(
-        full, n_full, fresh, n_fresh, splits, tiles, dm);
+        full, n_full, fresh, n_fresh, splits, tiles, dm, d_tiles);
     k_count_new<K><<<(unsigned)count_grid, kDT, smem_count, c.st>>>(
         full, fresh, n_full, n_fresh, splits, corank, cnt, tiles, dm, (uint32_t)group);
   }

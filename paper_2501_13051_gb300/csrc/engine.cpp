@@ -1575,7 +1575,11 @@ struct cdl_engine {
       G.Fcap = gcap_f[G.rel];
       uint32_t bits[kMaxK];
       for (uint32_t k = 0; k < R.arity; ++k) bits[k] = bits_of(R.bound[k]);
-      G.plan = make_radix_plan(R.arity, bits, radix_bits, 512);
+      // small capacities: 10-bit digits where they save a pass (fewer graph nodes)
+      uint32_t total_bits = 0;
+      for (uint32_t k = 0; k < R.arity; ++k) total_bits += bits[k];
+      const bool wide = G.Ucap <= (1u << 18) && (total_bits + 9) / 10 < (total_bits + 7) / 8;
+      G.plan = make_radix_plan(R.arity, bits, wide ? 10 : radix_bits, 512);
       G.sorted_in_alt = G.plan.npass % 2 == 1;
       bool ok = true;
       for (int side = 0; side < 2; ++side) {
@@ -1668,9 +1672,7 @@ struct cdl_engine {
   // full / delta columns) from the device state.
   cudaError_t graph_round(const std::vector<int>& slot, cudaGraphConditionalHandle loop) {
     uint32_t* ovf = &g_ctl()->overflow;
-    cudaError_t e = cudaMemsetAsync(g_cursor(0), 0, 8 * grel.size(), st);
-    for (size_t s = 0; s < gstep.size() && e == cudaSuccess; ++s)
-      e = cudaMemsetAsync(g_step(s, 2), 0, 8, st);
+    cudaError_t e = cudaSuccess;  // the cursors start at 0 (zeroed state, then round_end)
     for (size_t s = 0; s < grec.size() && e == cudaSuccess; ++s) {
       const GStep& g = grec[s];
       GStepRes& S = gstep[s];
@@ -1689,8 +1691,6 @@ struct cdl_engine {
       uint64_t* cursor = g.last ? g_cursor(slot[g.head]) : g_step(s, 2);
       const ColsOut out = g.last ? H->fresh.out() : S.inter.out();
       e = join_count_scan(ctx, js, static_cast<uint64_t*>(S.off.p), g_step(s, 0), S.cws.p);
-      if (e == cudaSuccess && !g.filter)
-        e = claim_output(ctx, cursor, g_step(s, 0), g_step(s, 1), S.ocap, ovf);
       if (e == cudaSuccess)
         e = join_write(ctx, js, static_cast<const uint64_t*>(S.off.p), S.ocap, out, 0, cursor,
                        S.ocap, S.wws.p, S.wbytes, g_step(s, 0), g.filter ? nullptr : g_step(s, 1),
@@ -1721,7 +1721,7 @@ struct cdl_engine {
     }
     if (e == cudaSuccess)
       e = round_end(ctx, g_cur(), g_next(), (uint32_t)grel.size(), g_ctl(), g_round(), kGraphRounds,
-                    loop);
+                    loop, g_cursor(0), (uint32_t)grel.size(), g_step(0, 0), (uint32_t)gstep.size());
     return e;
   }
 

@@ -11,7 +11,8 @@ namespace {
 
 __global__ void k_round_end(GraphRel* cur, GraphRel* next, uint32_t nrel, GraphCtl* ctl,
                             uint64_t* per_round, uint64_t per_round_cap,
-                            cudaGraphConditionalHandle loop) {
+                            cudaGraphConditionalHandle loop, uint64_t* cursors, uint32_t ncur,
+                            uint64_t* steps, uint32_t nsteps) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (ctl->overflow) {  // cur holds the last complete round
     ctl->done = 2;
@@ -33,6 +34,8 @@ __global__ void k_round_end(GraphRel* cur, GraphRel* next, uint32_t nrel, GraphC
     ctl->done = 1;
   else if (ctl->max_iters && ctl->iterations > ctl->max_iters)
     ctl->done = 3;
+  for (uint32_t i = 0; i < ncur; ++i) cursors[i] = 0;  // the next round appends from 0
+  for (uint32_t s = 0; s < nsteps; ++s) steps[3 * s + 2] = 0;
   cudaGraphSetConditional(loop, ctl->done ? 0u : 1u);
 }
 
@@ -40,8 +43,10 @@ __global__ void k_round_end(GraphRel* cur, GraphRel* next, uint32_t nrel, GraphC
 
 cudaError_t round_end(Ctx& c, GraphRel* cur, GraphRel* next, uint32_t nrel, GraphCtl* ctl,
                       uint64_t* per_round, uint64_t per_round_cap,
-                      cudaGraphConditionalHandle loop) {
-  k_round_end<<<1, 32, 0, c.st>>>(cur, next, nrel, ctl, per_round, per_round_cap, loop);
+                      cudaGraphConditionalHandle loop, uint64_t* cursors, uint32_t ncur,
+                      uint64_t* steps, uint32_t nsteps) {
+  k_round_end<<<1, 32, 0, c.st>>>(cur, next, nrel, ctl, per_round, per_round_cap, loop, cursors,
+                                  ncur, steps, nsteps);
   return cudaGetLastError();
 }
 

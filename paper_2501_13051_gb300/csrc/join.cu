@@ -102,10 +102,21 @@ __device__ __forceinline__ uint64_t merge_split(const uint64_t* off, uint64_t n,
 
 // All blocks' splits at once, one thread per split, so that no block
 // waits on a chain of dependent global loads before its first useful one.
+// Inside a captured round an unfiltered join's output range is claimed here
+// too (thread 0): *d_base = *cursor, *cursor += the join's size, and a range
+// past cap raises *overflow.
 __global__ void k_write_splits(const uint64_t* __restrict__ off, uint64_t n, uint64_t total,
                                uint64_t* __restrict__ splits, uint64_t nblocks,
-                               const uint64_t* dn, const uint64_t* dtotal) {
+                               const uint64_t* dn, const uint64_t* dtotal,
+                               unsigned long long* cursor, uint64_t* d_base, uint64_t cap,
+                               uint32_t* overflow) {
   const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d_base && b == 0) {
+    const uint64_t b0 = *cursor, t = *dtotal;
+    *d_base = b0;
+    *cursor = b0 + t;
+    if (b0 + t > cap) atomicOr(overflow, 1u);
+  }
   if (dn) {  // sizes from device memory (nblocks was sized for the capacities)
     n = dev_size(dn, n);
     total = dev_size(dtotal, total);
@@ -149,7 +160,7 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
     if (threadIdx.x == 0) s_split[0] = merge_split(off, n_probe, total, d0);
     if (threadIdx.x == 32) s_split[1] = merge_split(off, n_probe, total, d1);
   }
-  // (a device-sized launch had its claim made by claim_output)
+  // (a device-sized launch had its range claimed by the split kernel)
   if (!FILTER && !dbase && blockIdx.x == 0 && threadIdx.x == 0)
     atomicAdd(cursor, (unsigned long long)total);
   __syncthreads();
@@ -453,7 +464,7 @@ size_t join_write_workspace(uint64_t n_probe, uint64_t total) {
 
 cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_t total,
                        ColsOut out, uint64_t base, uint64_t* d_cursor, uint64_t out_cap,
-                       void* ws, size_t ws_bytes, const uint64_t* d_total, const uint64_t* d_base,
+                       void* ws, size_t ws_bytes, const uint64_t* d_total, uint64_t* d_base,
                        uint32_t* d_soft_err) {
   if (total == 0 || j.n_probe == 0) return cudaSuccess;
   const uint64_t nm = j.n_probe + total;
@@ -463,7 +474,9 @@ cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_
   if (ws && ws_bytes >= join_write_workspace(j.n_probe, total)) {
     splits = static_cast<uint64_t*>(ws);
     k_write_splits<<<(unsigned)((blocks + 1 + 255) / 256), 256, 0, c.st>>>(
-        d_off, j.n_probe, total, splits, blocks, j.dn, d_total);
+        d_off, j.n_probe, total, splits, blocks, j.dn, d_total,
+        reinterpret_cast<unsigned long long*>(d_cursor), d_base, out_cap,
+        d_soft_err ? d_soft_err : c.d_err);
   }
   // per probe row: two offsets, key, re-probed slot, its own head columns;
   // per output: the gathered build columns and the written head columns
@@ -483,26 +496,6 @@ cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_
   else
     k_join_write<false><<<(unsigned)blocks, kJT, 0, c.st>>>(j, d_off, total, out, base, cur,
                                                            out_cap, splits, err, d_total, d_base);
-  return cudaGetLastError();
-}
-
-namespace {
-// One thread: the unfiltered join's output range [*cursor, *cursor + total)
-// is claimed and its start stored; a range past cap raises *overflow.
-__global__ void k_claim(unsigned long long* cursor, const uint64_t* total, uint64_t* base,
-                        uint64_t cap, uint32_t* overflow) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const uint64_t b = *cursor, t = *total;
-  *base = b;
-  *cursor = b + t;
-  if (b + t > cap) atomicOr(overflow, 1u);
-}
-}  // namespace
-
-cudaError_t claim_output(Ctx& c, uint64_t* d_cursor, const uint64_t* d_total, uint64_t* d_base,
-                         uint64_t cap, uint32_t* d_overflow) {
-  k_claim<<<1, 32, 0, c.st>>>(reinterpret_cast<unsigned long long*>(d_cursor), d_total, d_base, cap,
-                              d_overflow);
   return cudaGetLastError();
 }
 

@@ -135,17 +135,15 @@ cudaError_t join_count_scan(Ctx& c, const JoinSpec& j, uint64_t* d_off, uint64_t
 // split, computed up front; without it each block searches for its own.
 size_t join_write_workspace(uint64_t n_probe, uint64_t total);
 // Inside a captured round: d_total (the join size, total then being its
-// capacity) and d_base (the start claimed by claim_output, unfiltered
-// joins) come from device memory, and a write past out_cap raises
-// *d_soft_err instead of the engine's error word.
+// capacity) comes from device memory; an unfiltered join claims its range
+// at *d_cursor first and keeps its start in *d_base (which needs ws); a
+// write or claim past out_cap raises *d_soft_err instead of the engine's
+// error word.
 cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_t total,
                        ColsOut out, uint64_t base, uint64_t* d_cursor, uint64_t out_cap,
                        void* ws, size_t ws_bytes, const uint64_t* d_total = nullptr,
-                       const uint64_t* d_base = nullptr, uint32_t* d_soft_err = nullptr);
-// *d_base = *d_cursor; *d_cursor += *d_total; *d_overflow = 1 when the range
-// passes cap (one thread).
-cudaError_t claim_output(Ctx& c, uint64_t* d_cursor, const uint64_t* d_total, uint64_t* d_base,
-                         uint64_t cap, uint32_t* d_overflow);
+                       uint64_t* d_base = nullptr, uint32_t* d_soft_err = nullptr);
+
 
 // -------------------------------------------------------------------- sort
 // Digit plan of an LSD radix sort over the packed key of K columns.
@@ -244,9 +242,12 @@ struct GraphCtl {
 // loop stops (cur still holds the last complete round); else next.nF =
 // cur.nF + next.nD, per_round[round] = sum of next.nD, cur <-> next, and the
 // loop's condition is set to continue while the round derived something.
+// It also zeroes the next round's cursors: `ncur` words at `cursors` and
+// every third word from `steps` + 2, `nsteps` of them.
 cudaError_t round_end(Ctx& c, GraphRel* cur, GraphRel* next, uint32_t nrel, GraphCtl* ctl,
                       uint64_t* per_round, uint64_t per_round_cap,
-                      cudaGraphConditionalHandle loop);
+                      cudaGraphConditionalHandle loop, uint64_t* cursors, uint32_t ncur,
+                      uint64_t* steps, uint32_t nsteps);
 // bounds[i] (i = 0..n_instances) = first row of the sorted column inst whose
 // value is >= i: instance i occupies rows [bounds[i], bounds[i + 1]).
 cudaError_t instance_bounds(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,

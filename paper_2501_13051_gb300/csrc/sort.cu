@@ -37,12 +37,15 @@ __device__ __forceinline__ uint32_t digit_of(const uint32_t (&v)[K], const PassP
 template <int K, int BITS, int T>
 __global__ void __launch_bounds__(T) k_radix_upsweep(ColsIn in, uint64_t n, PassP p,
                                                      uint32_t* __restrict__ tile_hist,
-                                                     uint64_t ntiles, const uint64_t* dn) {
+                                                     uint64_t ntiles, const uint64_t* dn,
+                                                     uint64_t* d_cells) {
   constexpr int R = 1 << BITS;
   constexpr int kRT = T, kRTile = T * kRItems;
   if (dn) {  // device-given size: the grid covers the capacity
     n = dev_size(dn, n);
     ntiles = (n + kRTile - 1) / kRTile;
+    // the length of the digit-major counts the pass's scan covers
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_cells = (uint64_t)R * ntiles;
     if (blockIdx.x >= ntiles) return;
   }
   __shared__ uint32_t h[R];
@@ -185,12 +188,6 @@ __global__ void k_column_max(ColsIn in, uint32_t k, uint64_t n, uint32_t* d_max)
   }
 }
 
-// R x tiles of the device-given size: the length of the digit-major count
-// array the pass's scan covers.
-__global__ void k_cells(const uint64_t* dn, uint64_t cap, uint64_t tile, uint64_t R, uint64_t* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = R * ((dev_size(dn, cap) + tile - 1) / tile);
-}
-
 template <int K, int BITS, int T>
 cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t n, void* ws,
                         bool* in_b, const uint64_t* dn) {
@@ -202,11 +199,8 @@ cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uin
   uint64_t* off = reinterpret_cast<uint64_t*>(static_cast<char*>(ws) +
                                               ((cells * 4 + 255) & ~uint64_t(255)));
   void* scan_ws = reinterpret_cast<char*>(off) + ((cells * 8 + 255) & ~uint64_t(255));
-  uint64_t* d_cells = nullptr;  // device-sized: scan length, after the scan's workspace
-  if (dn) {
-    d_cells = reinterpret_cast<uint64_t*>(static_cast<char*>(scan_ws) + scan_workspace(cells));
-    k_cells<<<1, 32, 0, c.st>>>(dn, n, kRTile, R, d_cells);
-  }
+  uint64_t* d_cells = nullptr;  // device-sized: scan length (the upsweep writes it)
+  if (dn) d_cells = reinterpret_cast<uint64_t*>(static_cast<char*>(scan_ws) + scan_workspace(cells));
   const size_t smem = sizeof(uint32_t) * K * kRTile;
   cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<K, BITS, T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -232,7 +226,8 @@ cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uin
     if (!single) {
       {
         ProfScope ps(c, kRadixUpsweep, 4.0 * cols_used * n + 4.0 * cells);
-        k_radix_upsweep<K, BITS, T><<<(unsigned)ntiles, kRT, 0, c.st>>>(in, n, p, hist, ntiles, dn);
+        k_radix_upsweep<K, BITS, T><<<(unsigned)ntiles, kRT, 0, c.st>>>(in, n, p, hist, ntiles, dn,
+                                                                        d_cells);
       }
       e = exclusive_scan(c, hist, cells, off, nullptr, scan_ws, d_cells);
       if (e != cudaSuccess) return e;
