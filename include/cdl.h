@@ -137,8 +137,10 @@ cdl_status cdl_relation_create(cdl_engine* e, const char* name, uint32_t arity, 
 
 /* Adds n tuples to relation rel: cols[k] points to n uint32 values of column
  * k (host memory if on_device == 0, device memory otherwise).  The library
- * copies the values; repeats are dropped.  Must precede cdl_run.
- * Returns CDL_E_VALUE if a value is 0xFFFFFFFF (nothing is added then). */
+ * copies and checks the values; repeats are dropped.  Must precede cdl_run.
+ * Returns CDL_E_VALUE if a value is 0xFFFFFFFF (nothing is added then).
+ * The sort and merge into the relation happen, for every relation loaded
+ * since, at the next call that reads relations (cdl_run, size, export). */
 cdl_status cdl_relation_load(cdl_engine* e, cdl_rel rel, const uint32_t* const* cols,
                              uint64_t n, int on_device);
 

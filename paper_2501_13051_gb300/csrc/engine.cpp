@@ -250,6 +250,7 @@ struct Relation {
   uint32_t arity = 0;
   bool idb = false;
   DCols full, delta, fresh;
+  std::vector<DCols> pending;  // checked loads not yet sorted into full
   uint64_t fresh_ub = 0;
   bool fresh_overflow = false;  // a predicted join of this round claimed past fresh.cap
   uint32_t bound[kMaxK] = {0, 0, 0, 0};  // every value of column k is <= bound[k]
@@ -1813,6 +1814,8 @@ struct cdl_engine {
 
   cdl_status run(cdl_stats* stats) {
     if (ran) return fail(CDL_E_STATE, "cdl_run was already called");
+    cdl_status fl = flush_loads();
+    if (fl != CDL_OK) return fl;
     ran = true;
     for (auto& r : rels) r->idb = false;
     for (const RuleR& rule : rules) rels[rule.head.rel]->idb = true;
@@ -2118,18 +2121,126 @@ struct cdl_engine {
       return r;
     }
     const uint32_t* hmax = reinterpret_cast<const uint32_t*>(h_ctl + kSlotScratch + 1);
-    uint32_t bits[kMaxK];
-    for (uint32_t k = 0; k < R.arity; ++k) {
-      R.bound[k] = std::max(R.bound[k], hmax[k]);
-      bits[k] = bits_of(hmax[k]);
+    for (uint32_t k = 0; k < R.arity; ++k) R.bound[k] = std::max(R.bound[k], hmax[k]);
+    R.pending.push_back(std::move(in));  // sorted and merged with the others by flush_loads
+    return CDL_OK;
+  }
+
+  // Sorts every relation's checked loads and merges them into its full
+  // version (repeats dropped), all relations back to back with one read-back
+  // of the sizes at the end.
+  // Many relations of one arity loaded into empty relations are sorted and
+  // deduplicated as one: a leading column numbers the relation of every
+  // tuple, so one sort and one unique pass replace one of each per
+  // relation, and the relations' rows are contiguous segments of the result.
+  cdl_status flush_group(const std::vector<uint32_t>& grp, uint32_t k) {
+    const uint32_t ng = (uint32_t)grp.size();
+    std::vector<uint64_t> off{0};
+    for (uint32_t i : grp) {
+      uint64_t n = 0;
+      for (const DCols& p : rels[i]->pending) n += p.n;
+      off.push_back(off.back() + n);
     }
-    r = sort_cols(in, bits);
+    const uint64_t N = off.back();
+    if (N == 0 || N > 0xFFFFFFFFull) return CDL_OK;  // left to the relation-by-relation path
+    DCols comb;
+    DBuf doff = alloc(8 * off.size());
+    if (!alloc_cols(comb, k + 1, N) || !doff.p) return fail(CDL_E_NOMEM, "grouped load");
+    comb.n = N;
+    cudaError_t e = cudaMemcpyAsync(doff.p, off.data(), 8 * off.size(), cudaMemcpyHostToDevice, st);
+    for (uint32_t g = 0; g < ng && e == cudaSuccess; ++g) {
+      uint64_t at = off[g];
+      for (const DCols& p : rels[grp[g]]->pending) {
+        for (uint32_t c = 0; c < k && e == cudaSuccess; ++c)
+          e = cudaMemcpyAsync(comb.c[c + 1] + at, p.c[c], 4 * p.n, cudaMemcpyDeviceToDevice, st);
+        at += p.n;
+      }
+    }
+    if (e == cudaSuccess)
+      e = fill_segments(ctx, comb.c[0], static_cast<const uint64_t*>(doff.p), ng, N);
+    if (e != cudaSuccess) return cuda_fail(e, "grouped load");
+    for (uint32_t i : grp) rels[i]->pending.clear();
+    uint32_t bits[kMaxK] = {bits_of(ng - 1), 0, 0, 0};
+    for (uint32_t i : grp)
+      for (uint32_t c = 0; c < k; ++c) bits[c + 1] = std::max(bits[c + 1], bits_of(rels[i]->bound[c]));
+    cdl_status r = sort_cols(comb, bits);
     if (r != CDL_OK) return r;
-    r = merge_into(R, in, nullptr, kSlotScratch);
-    if (r != CDL_OK) return r;
+    DCols uniq;
+    DBuf ws = alloc(diff_merge_workspace(0, N));
+    if (!alloc_cols(uniq, k + 1, N) || !ws.p) return fail(CDL_E_NOMEM, "grouped load");
+    e = diff_merge(ctx, k + 1, ColsIn{}, 0, comb.in(), N, uniq.out(), ColsOut{}, dslot(kSlotScratch),
+                   ws.p);
+    if (e != cudaSuccess) return cuda_fail(e, "grouped load");
     r = fetch(kSlotScratch, 1);
     if (r != CDL_OK) return r;
-    R.full.n += h_ctl[kSlotScratch];
+    const uint64_t nu = h_ctl[kSlotScratch];
+    comb.clear();
+    DBuf db = alloc(8 * (ng + 1));
+    if (!db.p) return fail(CDL_E_NOMEM, "grouped load");
+    std::vector<uint64_t> b(ng + 1);
+    e = instance_bounds(ctx, uniq.c[0], nu, ng, static_cast<uint64_t*>(db.p));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.data(), db.p, 8 * b.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "grouped load");
+    for (uint32_t g = 0; g < ng; ++g) {
+      Relation& R = *rels[grp[g]];
+      const uint64_t cnt = b[g + 1] - b[g];
+      if (!alloc_cols(R.full, k, std::max<uint64_t>(cnt, 1))) return fail(CDL_E_NOMEM, "grouped load");
+      for (uint32_t c = 0; c < k && cnt; ++c) {
+        e = cudaMemcpyAsync(R.full.c[c], uniq.c[c + 1] + b[g], 4 * cnt, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "grouped load");
+      }
+      R.full.n = cnt;
+      R.version[kFull]++;
+    }
+    evict_stale();
+    return CDL_OK;
+  }
+
+  cdl_status flush_loads() {
+    for (uint32_t k = 1; k < (uint32_t)kMaxK; ++k) {  // groups of eight or more relations
+      std::vector<uint32_t> grp;
+      for (uint32_t i = 0; i < rels.size(); ++i) {
+        const Relation& R = *rels[i];
+        if (R.arity == k && !R.pending.empty() && R.full.n == 0) grp.push_back(i);
+      }
+      if (grp.size() < 8) continue;
+      cdl_status r = flush_group(grp, k);
+      if (r != CDL_OK) return r;
+    }
+    std::vector<uint32_t> done;
+    for (uint32_t i = 0; i < rels.size(); ++i) {
+      Relation& R = *rels[i];
+      if (R.pending.empty()) continue;
+      DCols in;
+      if (R.pending.size() == 1) {
+        in = std::move(R.pending[0]);
+      } else {  // several loads: one buffer
+        uint64_t n = 0;
+        for (const DCols& p : R.pending) n += p.n;
+        if (!alloc_cols(in, R.arity, n)) return fail(CDL_E_NOMEM, "load buffer");
+        uint64_t at = 0;
+        for (const DCols& p : R.pending) {
+          for (uint32_t k = 0; k < R.arity; ++k) {
+            cudaError_t e = cudaMemcpyAsync(in.c[k] + at, p.c[k], 4 * p.n, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "load copy");
+          }
+          at += p.n;
+        }
+        in.n = n;
+      }
+      R.pending.clear();
+      uint32_t bits[kMaxK];
+      for (uint32_t k = 0; k < R.arity; ++k) bits[k] = bits_of(R.bound[k]);
+      cdl_status r = sort_cols(in, bits);
+      if (r == CDL_OK) r = merge_into(R, in, nullptr, kSlotDelta + i);
+      if (r != CDL_OK) return r;
+      done.push_back(i);
+    }
+    if (done.empty()) return CDL_OK;
+    cdl_status r = fetch(kSlotDelta, (uint32_t)rels.size());
+    if (r != CDL_OK) return r;
+    for (uint32_t i : done) rels[i]->full.n += h_ctl[kSlotDelta + i];
     evict_stale();
     return CDL_OK;
   }
@@ -2262,6 +2373,8 @@ cdl_status cdl_run(cdl_engine* e, cdl_stats* stats) {
 cdl_status cdl_relation_size(cdl_engine* e, cdl_rel rel, uint64_t* n) {
   if (!e || !n) return CDL_E_INVALID;
   if (rel >= e->rels.size()) return e->fail(CDL_E_INVALID, "no such relation");
+  const cdl_status f = e->flush_loads();
+  if (f != CDL_OK) return f;
   *n = e->rels[rel]->full.n;
   return CDL_OK;
 }
@@ -2270,6 +2383,8 @@ cdl_status cdl_relation_export(cdl_engine* e, cdl_rel rel, uint32_t* const* cols
                                uint64_t* n_written, int on_device) {
   if (!e || !n_written) return CDL_E_INVALID;
   if (rel >= e->rels.size()) return e->fail(CDL_E_INVALID, "no such relation");
+  const cdl_status f = e->flush_loads();
+  if (f != CDL_OK) return f;
   const Relation& R = *e->rels[rel];
   *n_written = R.full.n;
   if (cap < R.full.n) return e->fail(CDL_E_CAPACITY, "export buffer too small");
@@ -2297,6 +2412,8 @@ cdl_status cdl_relation_export_rows(cdl_engine* e, cdl_rel rel, uint64_t first, 
                                     uint32_t* const* cols, int on_device) {
   if (!e) return CDL_E_INVALID;
   if (rel >= e->rels.size()) return e->fail(CDL_E_INVALID, "no such relation");
+  const cdl_status f = e->flush_loads();
+  if (f != CDL_OK) return f;
   const Relation& R = *e->rels[rel];
   if (first > R.full.n || count > R.full.n - first)
     return e->fail(CDL_E_CAPACITY, "row range past the relation");

@@ -248,6 +248,10 @@ cudaError_t round_end(Ctx& c, GraphRel* cur, GraphRel* next, uint32_t nrel, Grap
                       uint64_t* per_round, uint64_t per_round_cap,
                       cudaGraphConditionalHandle loop, uint64_t* cursors, uint32_t ncur,
                       uint64_t* steps, uint32_t nsteps);
+// col[j] = s for the rows j of segment s: [off[s], off[s + 1]), off having
+// nseg + 1 device entries and off[nseg] = total.
+cudaError_t fill_segments(Ctx& c, uint32_t* col, const uint64_t* off, uint32_t nseg,
+                          uint64_t total);
 // bounds[i] (i = 0..n_instances) = first row of the sorted column inst whose
 // value is >= i: instance i occupies rows [bounds[i], bounds[i + 1]).
 cudaError_t instance_bounds(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,

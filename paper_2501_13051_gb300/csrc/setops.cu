@@ -150,6 +150,33 @@ __global__ void __launch_bounds__(kGT) k_gather_segments(ColsIn a, ColsIn b, uin
 
 }  // namespace
 
+// col[j] = s for every row j of segment s (rows [off[s], off[s + 1])).
+__global__ void k_fill_segments(uint32_t* __restrict__ col, const uint64_t* __restrict__ off,
+                                uint32_t nseg, uint64_t total) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total;
+       j += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = nseg;  // the last segment starting at or before j
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(off + mid) <= j)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    col[j] = lo;
+  }
+}
+
+cudaError_t fill_segments(Ctx& c, uint32_t* col, const uint64_t* off, uint32_t nseg,
+                          uint64_t total) {
+  if (total == 0 || nseg == 0) return cudaSuccess;
+  ProfScope p(c, kMisc, 4.0 * total);
+  uint64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_fill_segments<<<(unsigned)blocks, 256, 0, c.st>>>(col, off, nseg, total);
+  return cudaGetLastError();
+}
+
 cudaError_t instance_bounds(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,
                             uint64_t* bounds) {
   ProfScope p(c, kRetire, 8.0 * (n_instances + 1));
