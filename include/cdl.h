@@ -118,6 +118,11 @@ typedef struct {
                            runs on the host, then the graph is rebuilt larger); other
                            programs run as with 0.  Values >= 2: the same, with buffers
                            starting at that many rows instead of 65,536 */
+  int32_t dense_bits;   /* a derived relation (not batched) whose columns need T <= dense_bits
+                           bits in all keeps its new tuples of a round as a bitmap of 2^T
+                           bits: join outputs set bits instead of being written, and the
+                           bits read back in order are the sorted unique tuples (no radix
+                           sort).  0 = default 28; -1 = never.  Results never depend on it */
 } cdl_options;
 
 /* Fills *opts with the defaults (everything zero / NULL except the

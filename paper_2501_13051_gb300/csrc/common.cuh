@@ -131,6 +131,48 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* smem, T* total) {
   return res;
 }
 
+// A relation of arity k whose columns need T = bits_0 + ... + bits_{k-1}
+// bits in all can also be held as a bitmap of 2^T bits: tuple (v_0..v_{k-1})
+// is bit sum_k v_k << shift_k, with shift_k the bits of the columns after k.
+// Increasing bit order is then the tuples' lexicographic order, and setting
+// a bit twice is a no-op, so the bitmap is a sorted set.
+struct DenseSet {
+  uint32_t* words;  // nbits / 32 words (at least one)
+  uint64_t nbits;   // 2^T
+  uint32_t k;
+  uint32_t shift[kMaxK];
+  uint32_t mask[kMaxK];  // 2^bits_k - 1
+};
+
+// Sets the tuples' bits, one atomic per distinct word among a warp's
+// lanes.  Every lane of the warp calls it (keep = the lane has a tuple);
+// a tuple outside the bitmap raises kErrCapacity and sets nothing.
+__device__ __forceinline__ void dense_set_bits(const DenseSet& d, const uint32_t (&v)[kMaxK],
+                                               bool keep, uint32_t* err) {
+  uint64_t idx = 0;
+  bool out = false;
+#pragma unroll
+  for (int k = 0; k < kMaxK; ++k)
+    if (k < (int)d.k) {
+      idx |= (uint64_t)v[k] << d.shift[k];
+      out |= v[k] > d.mask[k];
+    }
+  if (keep && (out || idx >= d.nbits)) {
+    atomicOr(err, kErrCapacity);
+    keep = false;
+  }
+  const uint32_t word = (uint32_t)(idx >> 5), bit = 1u << (idx & 31);
+  // Bits only go from 0 to 1 while tuples are added, so a bit seen set (in
+  // a value read at any time, from L1 or L2) is set: only the others need
+  // an atomic.  Repeated join outputs mostly end here.
+  if (keep) keep = (d.words[word] & bit) == 0u;
+  const uint32_t act = __ballot_sync(0xffffffffu, keep);
+  if (!keep) return;
+  const uint32_t grp = __match_any_sync(act, word);
+  const uint32_t bits = __reduce_or_sync(grp, bit);
+  if (lane_id() == (uint32_t)(__ffs(grp) - 1)) atomicOr(d.words + word, bits);
+}
+
 // Device-sized launches (a round captured in a CUDA graph): the grid is
 // sized for a capacity known to the host, the actual size is read from
 // device memory and clamped to that capacity, so no access can leave the

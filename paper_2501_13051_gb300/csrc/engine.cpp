@@ -259,6 +259,14 @@ struct Relation {
   // full for this buffer (instance i: ret_cnt[i] rows from ret_off[i])
   DCols retired;
   std::vector<uint64_t> ret_off, ret_cnt;
+  // dense form (a tuple space of at most 2^dense_bits): the hash joins of a
+  // round set the bits of their tuples in dset; at the round's end the rows
+  // written to fresh join them, and dense_rows takes the bits back out as
+  // sorted unique rows
+  DenseSet dset{};
+  DBuf dset_buf;
+  uint64_t dense_ub = 0;  // tuples sent to dset this round: a bound on its bits
+  DCols dense_rows;
 };
 
 struct Term {
@@ -309,7 +317,6 @@ struct Src {
 
 constexpr uint32_t kMaxRels = 1024;
 // control block slots (uint64): 0 error word, 1 scratch, 2 aux cursor,
-// 4 + r fresh cursor of relation r, 4 + kMaxRels + r delta size of r
 // 3 single-pass join size, 4 overflow flag, 5 overflow flag of the round's
 // deferred checks, 8 + r fresh cursor of relation r,
 // 8 + kMaxRels + r delta size of relation r
@@ -354,6 +361,7 @@ struct cdl_engine {
   static constexpr uint32_t kMaxDeferred = 4096;
   static constexpr double kDirectMaxTuples = double(1 << 24);
   static constexpr uint64_t kPredictMinRows = 1 << 15;  // smaller probes keep the count pass
+  static constexpr int kDenseBits = 28;  // default bound of a dense relation's tuple space (32 MB)
   struct Deferred {
     std::tuple<size_t, size_t, size_t> step;
     uint32_t head = 0;  // relation the join appends to
@@ -1001,7 +1009,9 @@ struct cdl_engine {
       // features of this join, for the estimator's prediction and its log
       const std::tuple<size_t, size_t, size_t> step_key{(size_t)(&rule - rules.data()), start, t};
       // a prediction pays off where the count pass it saves is not trivial
+      // (a dense head needs no buffer sized: its tuples become bits)
       const bool predict = ix != nullptr && est_ready() && !force_exact &&
+                           !(last && rels[rule.head.rel]->dset.words) &&
                            P.n >= (opt.est_min_rows ? opt.est_min_rows : kPredictMinRows);
       const bool feats = ix != nullptr && (predict || opt.estimator >= 2);
       if (feats) {
@@ -1157,6 +1167,14 @@ struct cdl_engine {
       const size_t wws = join_write_workspace(P.n, total);
       DBuf wsp = alloc(wws);
       if (!wsp.p) return fail(CDL_E_NOMEM, "join splits");
+      if (last && rels[rule.head.rel]->dset.words) {  // a dense head: bits, not rows
+        Relation& H = *rels[rule.head.rel];
+        H.dense_ub += total;
+        e = join_write(ctx, js, static_cast<const uint64_t*>(off.p), total, ColsOut{}, 0, nullptr,
+                       0, wsp.p, wws, nullptr, nullptr, nullptr, &H.dset);
+        if (e != cudaSuccess) return cuda_fail(e, "join write");
+        return CDL_OK;
+      }
       if (last) {
         Relation& H = *rels[rule.head.rel];
         H.fresh_ub = h_ctl[kSlotCursor + rule.head.rel];
@@ -1205,6 +1223,37 @@ struct cdl_engine {
       vers[i] = kDelta;
       cdl_status r = nb == 1 ? eval_copy(rule, kDelta) : eval_join(rule, vers, i);
       if (r != CDL_OK) return r;
+    }
+    return CDL_OK;
+  }
+
+  // Derived relations whose tuple space has at most 2^dense_bits tuples (not
+  // batched) get a bitmap of that space, empty between rounds.
+  cdl_status setup_dense() {
+    const int dmax = opt.dense_bits == 0 ? kDenseBits : opt.dense_bits;
+    for (auto& rp : rels) {
+      Relation& R = *rp;
+      R.dset = DenseSet{};
+      R.dset_buf.reset();
+      R.dense_rows.clear();
+      if (!R.idb || opt.n_instances || dmax <= 0 || R.arity == 0) continue;
+      uint32_t bits[kMaxK], T = 0;
+      for (uint32_t k = 0; k < R.arity; ++k) T += bits[k] = bits_of(R.bound[k]);
+      if (T > (uint32_t)std::min(dmax, 30)) continue;
+      const uint64_t nw = T >= 5 ? (1ull << (T - 5)) : 1;
+      R.dset_buf = alloc(4 * nw);
+      if (!R.dset_buf.p) return fail(CDL_E_NOMEM, "dense set");
+      cudaError_t e = cudaMemsetAsync(R.dset_buf.p, 0, 4 * nw, st);
+      if (e != cudaSuccess) return cuda_fail(e, "dense set");
+      R.dset.words = static_cast<uint32_t*>(R.dset_buf.p);
+      R.dset.nbits = 1ull << T;
+      R.dset.k = R.arity;
+      uint32_t sh = 0;
+      for (int k = (int)R.arity - 1; k >= 0; --k) {
+        R.dset.shift[k] = sh;
+        R.dset.mask[k] = (uint32_t)((1ull << bits[k]) - 1);
+        sh += bits[k];
+      }
     }
     return CDL_OK;
   }
@@ -1428,6 +1477,39 @@ struct cdl_engine {
     }
   }
 
+  // Dense relations at a round's end: the rows written to fresh (copies,
+  // single-pass joins) set their bits too, then the bits come out as the
+  // round's sorted unique new rows, whose numbers are read back at once.
+  cdl_status extract_dense() {
+    const uint32_t nr = (uint32_t)rels.size();
+    bool any = false;
+    for (uint32_t i = 0; i < nr; ++i) {
+      Relation& R = *rels[i];
+      R.dense_rows.clear();
+      if (!R.idb || !R.dset.words) continue;
+      const uint64_t nf = std::min<uint64_t>(h_ctl[kSlotCursor + i], R.fresh.cap);
+      if (nf == 0 && R.dense_ub == 0) continue;
+      const uint64_t cap = std::min<uint64_t>(R.dset.nbits, nf + R.dense_ub);
+      DBuf ws = alloc(dense_extract_workspace(R.dset.nbits));
+      if (!alloc_cols(R.dense_rows, R.arity, cap) || !ws.p) return fail(CDL_E_NOMEM, "dense rows");
+      cudaError_t e = dense_insert(ctx, R.dset, R.fresh.in(), nf);
+      if (e == cudaSuccess)
+        e = dense_extract(ctx, R.dset, R.dense_rows.out(), cap, dslot(kSlotDelta + i), ws.p);
+      if (e != cudaSuccess) return cuda_fail(e, "dense rows");
+      any = true;
+    }
+    if (!any) return CDL_OK;
+    cdl_status r = fetch(kSlotDelta, nr);
+    if (r != CDL_OK) return r;
+    for (uint32_t i = 0; i < nr; ++i) {
+      Relation& R = *rels[i];
+      if (!R.dense_rows.buf.p) continue;
+      R.dense_rows.n = h_ctl[kSlotDelta + i];
+      prof.add_bytes(kDense, 4.0 * R.arity * R.dense_rows.n);
+    }
+    return CDL_OK;
+  }
+
   // Every rule once; then the cursors (and the deferred joins' sizes) are
   // read back.  A relation whose predicted joins claimed past its buffer has
   // only appended to that buffer: its rules run again, exact, from an empty
@@ -1443,6 +1525,7 @@ struct cdl_engine {
     for (auto& r : rels) {
       r->fresh_ub = 0;
       r->fresh_overflow = false;
+      r->dense_ub = 0;
     }
     for (const RuleR& rule : rules) {
       cdl_status s = eval_rule(rule, round == 1);
@@ -1820,6 +1903,8 @@ struct cdl_engine {
     for (auto& r : rels) r->idb = false;
     for (const RuleR& rule : rules) rels[rule.head.rel]->idb = true;
     propagate_bounds();
+    cdl_status ds = setup_dense();
+    if (ds != CDL_OK) return ds;
     prof.reset();
     joins = 0;
     cudaEvent_t t0, t1;
@@ -1866,7 +1951,9 @@ struct cdl_engine {
       recording = opt.graph && round == first_semi;  // the first semi-naive round is the plan
       status = eval_round(round);
       recording = false;
+      if (status == CDL_OK) status = extract_dense();
       if (status != CDL_OK) break;
+      std::vector<uint8_t> merged(nr, 0);
       for (uint32_t i = 0; i < nr; ++i) {
         Relation& R = *rels[i];
         if (!R.idb) continue;
@@ -1879,6 +1966,18 @@ struct cdl_engine {
           status = cuda_fail(e, "delta reset");
           break;
         }
+        if (R.dset.words) {  // the dense form: the round's rows come out sorted and unique
+          DCols rows = std::move(R.dense_rows);
+          if (rows.n == 0) continue;
+          if (R.full.n + rows.n > 0xFFFFFFFFull) {
+            status = fail(CDL_E_CAPACITY, "relation " + R.name + " would exceed 2^32 tuples");
+            break;
+          }
+          status = merge_into(R, rows, &R.delta, kSlotDelta + i);
+          if (status != CDL_OK) break;
+          merged[i] = 1;
+          continue;
+        }
         if (R.fresh.n == 0) continue;
         if (R.full.n + R.fresh.n > 0xFFFFFFFFull) {
           status = fail(CDL_E_CAPACITY, "relation " + R.name + " would exceed 2^32 tuples");
@@ -1890,6 +1989,7 @@ struct cdl_engine {
         if (status != CDL_OK) break;
         status = merge_into(R, R.fresh, &R.delta, kSlotDelta + i);
         if (status != CDL_OK) break;
+        merged[i] = 1;
       }
       if (status != CDL_OK) break;
       status = fetch(kSlotDelta, nr);
@@ -1898,10 +1998,10 @@ struct cdl_engine {
       for (uint32_t i = 0; i < nr; ++i) {
         Relation& R = *rels[i];
         if (!R.idb) continue;
-        const uint64_t nd = R.fresh.n ? h_ctl[kSlotDelta + i] : 0;
+        const uint64_t nd = merged[i] ? h_ctl[kSlotDelta + i] : 0;
         R.delta.n = nd;
         R.full.n += nd;
-        if (R.fresh.n) prof.add_bytes(kDiffMerge, 8.0 * R.arity * nd);
+        if (merged[i]) prof.add_bytes(kDiffMerge, 8.0 * R.arity * nd);
         new_total += nd;
         if (opt.n_instances && nd) {  // batched: instances that derived in this round
           cudaError_t e = mark_instances(ctx, R.delta.c[0], nd, opt.n_instances,

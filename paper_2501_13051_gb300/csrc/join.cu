@@ -134,13 +134,14 @@ __device__ __forceinline__ uint32_t ref_value(const JoinSpec& j, const ColsIn& p
   return r.v;
 }
 
-template <bool FILTER>
+// DENSE: each output tuple sets its bit in dset instead of being written.
+template <bool FILTER, bool DENSE>
 __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint64_t* __restrict__ off,
                                                     uint64_t total, ColsOut out, uint64_t base,
                                                     unsigned long long* cursor, uint64_t out_cap,
                                                     const uint64_t* __restrict__ splits,
                                                     uint32_t* err, const uint64_t* dtotal,
-                                                    const uint64_t* dbase) {
+                                                    const uint64_t* dbase, const DenseSet dset) {
   __shared__ uint64_t s_off[kJTile + 1];
   __shared__ uint32_t s_start[kJTile + 1];
   __shared__ uint64_t s_split[2];
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
     if (threadIdx.x == 32) s_split[1] = merge_split(off, n_probe, total, d1);
   }
   // (a device-sized launch had its range claimed by the split kernel)
-  if (!FILTER && !dbase && blockIdx.x == 0 && threadIdx.x == 0)
+  if (!FILTER && !DENSE && !dbase && blockIdx.x == 0 && threadIdx.x == 0)
     atomicAdd(cursor, (unsigned long long)total);
   __syncthreads();
   const uint64_t j0 = s_split[0], j1 = s_split[1];
@@ -206,6 +207,10 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
           keep &= ref_value(j, probe, j.neq[q][0], row, brow) !=
                   ref_value(j, probe, j.neq[q][1], row, brow);
       }
+    }
+    if (DENSE) {  // the loop's trip count is the block's: every lane is here
+      dense_set_bits(dset, vals, keep, err);
+      continue;
     }
     uint64_t pos;
     if (FILTER) {
@@ -465,7 +470,7 @@ size_t join_write_workspace(uint64_t n_probe, uint64_t total) {
 cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_t total,
                        ColsOut out, uint64_t base, uint64_t* d_cursor, uint64_t out_cap,
                        void* ws, size_t ws_bytes, const uint64_t* d_total, uint64_t* d_base,
-                       uint32_t* d_soft_err) {
+                       uint32_t* d_soft_err, const DenseSet* dense) {
   if (total == 0 || j.n_probe == 0) return cudaSuccess;
   const uint64_t nm = j.n_probe + total;
   const uint64_t blocks = (nm + kJTile - 1) / kJTile;
@@ -485,17 +490,25 @@ cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_
     nbuild += j.out[k].side == 1;
     nprobe += j.out[k].side == 0;
   }
+  // (a dense head's bits are set in L2-resident words, not written out)
   const double bytes = (16.0 + 4.0 + 16.0 + 4.0 * nprobe) * j.n_probe +
-                       (4.0 * nbuild + 4.0 * j.out_k) * total;
+                       (4.0 * nbuild + (dense ? 0.0 : 4.0 * j.out_k)) * total;
   ProfScope p(c, kJoinWrite, bytes);
   auto* cur = reinterpret_cast<unsigned long long*>(d_cursor);
   uint32_t* err = d_soft_err ? d_soft_err : c.d_err;
-  if (filter)
-    k_join_write<true><<<(unsigned)blocks, kJT, 0, c.st>>>(j, d_off, total, out, base, cur, out_cap,
-                                                          splits, err, d_total, d_base);
+  const DenseSet ds = dense ? *dense : DenseSet{};
+  if (dense && filter)
+    k_join_write<true, true><<<(unsigned)blocks, kJT, 0, c.st>>>(
+        j, d_off, total, out, base, cur, out_cap, splits, err, d_total, d_base, ds);
+  else if (dense)
+    k_join_write<false, true><<<(unsigned)blocks, kJT, 0, c.st>>>(
+        j, d_off, total, out, base, cur, out_cap, splits, err, d_total, d_base, ds);
+  else if (filter)
+    k_join_write<true, false><<<(unsigned)blocks, kJT, 0, c.st>>>(
+        j, d_off, total, out, base, cur, out_cap, splits, err, d_total, d_base, ds);
   else
-    k_join_write<false><<<(unsigned)blocks, kJT, 0, c.st>>>(j, d_off, total, out, base, cur,
-                                                           out_cap, splits, err, d_total, d_base);
+    k_join_write<false, false><<<(unsigned)blocks, kJT, 0, c.st>>>(
+        j, d_off, total, out, base, cur, out_cap, splits, err, d_total, d_base, ds);
   return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ enum KernelClass : int {
   kMlp,
   kJoinDirect,
   kRetire,
+  kDense,
   kNumClasses
 };
 const char* kernel_class_name(int c);
@@ -142,7 +143,20 @@ size_t join_write_workspace(uint64_t n_probe, uint64_t total);
 cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_t total,
                        ColsOut out, uint64_t base, uint64_t* d_cursor, uint64_t out_cap,
                        void* ws, size_t ws_bytes, const uint64_t* d_total = nullptr,
-                       uint64_t* d_base = nullptr, uint32_t* d_soft_err = nullptr);
+                       uint64_t* d_base = nullptr, uint32_t* d_soft_err = nullptr,
+                       const DenseSet* dense = nullptr);
+// (dense != null: each output tuple sets its bit in *dense instead of being
+// written; out, base, d_cursor and out_cap are then unused.)
+
+// -------------------------------------------------------------- dense sets
+// Bits of n rows set in d (a row outside d raises kErrCapacity).
+cudaError_t dense_insert(Ctx& c, const DenseSet& d, ColsIn rows, uint64_t n);
+size_t dense_extract_workspace(uint64_t nbits);
+// The set bits of d as rows in increasing bit order (lexicographic, no
+// repeats) into out (cap rows; more raise kErrCapacity); their number in
+// *d_count.  Clears d.
+cudaError_t dense_extract(Ctx& c, const DenseSet& d, ColsOut out, uint64_t cap,
+                          uint64_t* d_count, void* ws);
 
 
 // -------------------------------------------------------------------- sort

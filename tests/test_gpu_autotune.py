@@ -34,7 +34,8 @@ def test_tuning_runs_cover_every_candidate(cdl, oracle_lib, tmp_path):
     prog = W.sg_program(W.random_forest(5000, 21))
     want = oracle_lib.run_program(prog)
     for _ in range(8):  # each run measures the candidates not yet tried twice
-        got, st = cdl.run_program(prog, autotune=2, tune_cache=cache)
+        # sorted rows (dense_bits=-1): a bitmap of this tuple space needs no sort
+        got, st = cdl.run_program(prog, autotune=2, tune_cache=cache, dense_bits=-1)
         assert np.array_equal(got["sg"], want.relations["sg"])
         assert st.iterations == want.iterations
     rows = read_cache(cache)
@@ -44,7 +45,7 @@ def test_tuning_runs_cover_every_candidate(cdl, oracle_lib, tmp_path):
         assert sorted(rows[k]) == [0, 1, 2, 3], (k, rows[k])
         assert all(n >= 1 and c > 0 for n, c in rows[k].values())
     # cache mode reads the file and takes the cheapest candidates
-    got, st = cdl.run_program(prog, autotune=1, tune_cache=cache)
+    got, st = cdl.run_program(prog, autotune=1, tune_cache=cache, dense_bits=-1)
     assert np.array_equal(got["sg"], want.relations["sg"])
 
 
@@ -74,5 +75,5 @@ def test_unwritable_cache_file_is_reported(cdl, tmp_path):
     prog = W.tc_program(W.er_graph(1000, 1500, 6))  # sorts large enough to be timed
     bad = str(tmp_path / "no-such-dir" / "tune.txt")
     with pytest.raises(cdl.CdlError) as ex:
-        cdl.run_program(prog, autotune=2, tune_cache=bad)
+        cdl.run_program(prog, autotune=2, tune_cache=bad, dense_bits=-1)
     assert ex.value.name == "CDL_E_INVALID"

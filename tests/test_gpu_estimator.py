@@ -116,8 +116,9 @@ def test_predicted_joins_are_exact_and_cheaper(cdl, oracle_lib, trained, make):
     _, _, params, _ = trained
     prog = make()
     want = oracle_lib.run_program(prog)
-    exact, st0 = cdl.run_program(prog)
-    with cdl.Engine(estimator=1, est_params=params, est_min_rows=1) as e:
+    # sorted rows (dense_bits=-1): a bitmap head needs no predicted buffer
+    exact, st0 = cdl.run_program(prog, dense_bits=-1)
+    with cdl.Engine(estimator=1, est_params=params, est_min_rows=1, dense_bits=-1) as e:
         e.load_program(prog)
         st = e.run()
         got = {nm: e.export(nm) for nm in prog.arity}
@@ -134,7 +135,8 @@ def test_forced_underprediction_falls_back_exactly(cdl, oracle_lib, trained):
     _, _, params, _ = trained
     prog = W.sg_program(W.random_forest(5000, 11))
     want = oracle_lib.run_program(prog)
-    with cdl.Engine(estimator=1, est_params=params, est_margin=-40.0, est_min_rows=1) as e:
+    with cdl.Engine(estimator=1, est_params=params, est_margin=-40.0, est_min_rows=1,
+                    dense_bits=-1) as e:
         e.load_program(prog)
         st = e.run()
         got = e.export("sg")
@@ -183,9 +185,22 @@ def hot_key_program(with_filter):
 def test_hot_keys_through_the_single_pass_join(cdl, oracle_lib, with_filter):
     prog = hot_key_program(with_filter)
     want = oracle_lib.run_program(prog)
-    with cdl.Engine(estimator=1, est_params=constant_network(20.0), est_min_rows=1) as e:
+    with cdl.Engine(estimator=1, est_params=constant_network(20.0), est_min_rows=1,
+                    dense_bits=-1) as e:
         e.load_program(prog)
         st = e.run()
         got = e.export("out")
     assert np.array_equal(got, want.relations["out"])
     assert st.est_predictions > 0 and st.est_overflows == 0
+
+
+def test_dense_heads_take_no_prediction(cdl, oracle_lib):
+    """A head kept as a bitmap has no buffer to size: its joins keep the
+    exact count pass even with a network that predicts every join."""
+    prog = hot_key_program(False)
+    with cdl.Engine(estimator=1, est_params=constant_network(20.0), est_min_rows=1) as e:
+        e.load_program(prog)
+        st = e.run()
+        got = e.export("out")
+    assert np.array_equal(got, oracle_lib.run_program(prog).relations["out"])
+    assert st.est_predictions == 0

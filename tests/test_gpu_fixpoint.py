@@ -33,28 +33,47 @@ def check(cdl, oracle_lib, prog, **opts):
     return st
 
 
+# Every small-domain program below runs in both forms of the round's new
+# tuples: bitmaps of the tuple space (dense_bits default) and sorted rows.
+FORMS = pytest.mark.parametrize("dense", [0, -1], ids=["dense", "sorted"])
+
+
+@FORMS
 @pytest.mark.parametrize("n,m,seed", [(1000, 1500, 1), (1000, 1500, 11), (50, 120, 2), (400, 380, 3)])
-def test_transitive_closure(cdl, oracle_lib, n, m, seed):
-    check(cdl, oracle_lib, W.tc_program(W.er_graph(n, m, seed)))
+def test_transitive_closure(cdl, oracle_lib, n, m, seed, dense):
+    check(cdl, oracle_lib, W.tc_program(W.er_graph(n, m, seed)), dense_bits=dense)
 
 
+@FORMS
 @pytest.mark.parametrize("n,seed", [(2000, 2), (5000, 11)])
 @pytest.mark.parametrize("make", [W.sg_program, W.sg_paper_program])
-def test_same_generation(cdl, oracle_lib, n, seed, make):
-    check(cdl, oracle_lib, make(W.random_forest(n, seed)))
+def test_same_generation(cdl, oracle_lib, n, seed, make, dense):
+    check(cdl, oracle_lib, make(W.random_forest(n, seed)), dense_bits=dense)
 
 
-def test_points_to_scaled(cdl, oracle_lib):
-    check(cdl, oracle_lib, W.points_to_program(W.points_to_edb(1 / 2048, 3)))
+@FORMS
+def test_points_to_scaled(cdl, oracle_lib, dense):
+    check(cdl, oracle_lib, W.points_to_program(W.points_to_edb(1 / 2048, 3)), dense_bits=dense)
+
+
+@pytest.mark.parametrize("bits", [12, 21, 23])
+def test_dense_bound_just_fits(cdl, oracle_lib, bits):
+    """dense_bits below, between and above the tuple spaces of TC on 1,000
+    nodes (10 + 10 bits) and of the paper's SG on 2,000 nodes (11 + 11):
+    relations that fit are bitmaps, the others sorted rows."""
+    prog = W.sg_paper_program(W.random_forest(2000, 7))
+    check(cdl, oracle_lib, prog, dense_bits=bits)
+    check(cdl, oracle_lib, W.tc_program(W.er_graph(1000, 1500, 3)), dense_bits=bits)
 
 
 def test_owl_scaled(cdl, oracle_lib):
     check(cdl, oracle_lib, W.owl_program(*W.owl_triples(200_000, 4, n_entities=50_000)))
 
 
+@FORMS
 @pytest.mark.parametrize("seed", range(40))
-def test_random_programs(cdl, oracle_lib, seed):
-    check(cdl, oracle_lib, W.random_program(seed))
+def test_random_programs(cdl, oracle_lib, seed, dense):
+    check(cdl, oracle_lib, W.random_program(seed), dense_bits=dense)
 
 
 @pytest.mark.parametrize("opts", [dict(radix_bits=10), dict(hash_load=0.8), dict(timing=True)])
