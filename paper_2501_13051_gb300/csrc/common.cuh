@@ -144,11 +144,9 @@ struct DenseSet {
   uint32_t mask[kMaxK];  // 2^bits_k - 1
 };
 
-// Sets the tuples' bits, one atomic per distinct word among a warp's
-// lanes.  Every lane of the warp calls it (keep = the lane has a tuple);
-// a tuple outside the bitmap raises kErrCapacity and sets nothing.
-__device__ __forceinline__ void dense_set_bits(const DenseSet& d, const uint32_t (&v)[kMaxK],
-                                               bool keep, uint32_t* err) {
+// The word and bit of tuple v in d; false when v lies outside d.
+__device__ __forceinline__ bool dense_locate(const DenseSet& d, const uint32_t (&v)[kMaxK],
+                                             uint32_t* word, uint32_t* bit) {
   uint64_t idx = 0;
   bool out = false;
 #pragma unroll
@@ -157,20 +155,31 @@ __device__ __forceinline__ void dense_set_bits(const DenseSet& d, const uint32_t
       idx |= (uint64_t)v[k] << d.shift[k];
       out |= v[k] > d.mask[k];
     }
-  if (keep && (out || idx >= d.nbits)) {
-    atomicOr(err, kErrCapacity);
-    keep = false;
-  }
-  const uint32_t word = (uint32_t)(idx >> 5), bit = 1u << (idx & 31);
-  // Bits only go from 0 to 1 while tuples are added, so a bit seen set (in
-  // a value read at any time, from L1 or L2) is set: only the others need
-  // an atomic.  Repeated join outputs mostly end here.
-  if (keep) keep = (d.words[word] & bit) == 0u;
-  const uint32_t act = __ballot_sync(0xffffffffu, keep);
+  *word = (uint32_t)(idx >> 5);
+  *bit = 1u << (idx & 31);
+  return !out && idx < d.nbits;
+}
+
+// Bits only go from 0 to 1 while tuples are added, so a bit seen set (in a
+// value read at any time, from L1 or L2) is set: only a missing bit needs an
+// atomic.  Repeated outputs of a join mostly stop at the read.  (Merging a
+// warp's bits per word first, by match and reduce, costs more than it
+// saves: those warp instructions then bound the join's write pass.)
+__device__ __forceinline__ bool dense_missing(const DenseSet& d, uint32_t word, uint32_t bit) {
+  return (d.words[word] & bit) == 0u;
+}
+
+// Sets the bit of tuple v (keep = the thread has one); a tuple outside the
+// bitmap raises kErrCapacity and sets nothing.
+__device__ __forceinline__ void dense_set_bits(const DenseSet& d, const uint32_t (&v)[kMaxK],
+                                               bool keep, uint32_t* err) {
+  uint32_t word = 0, bit = 0;
   if (!keep) return;
-  const uint32_t grp = __match_any_sync(act, word);
-  const uint32_t bits = __reduce_or_sync(grp, bit);
-  if (lane_id() == (uint32_t)(__ffs(grp) - 1)) atomicOr(d.words + word, bits);
+  if (!dense_locate(d, v, &word, &bit)) {
+    atomicOr(err, kErrCapacity);
+    return;
+  }
+  if (dense_missing(d, word, bit)) atomicOr(d.words + word, bit);
 }
 
 // Device-sized launches (a round captured in a CUDA graph): the grid is

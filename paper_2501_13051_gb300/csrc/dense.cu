@@ -23,8 +23,6 @@ __host__ __device__ __forceinline__ uint64_t words_of(uint64_t nbits) {
 __global__ void __launch_bounds__(256) k_dense_insert(DenseSet d, ColsIn rows, uint64_t n,
                                                       uint32_t* err) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  // the loop bound depends on the block only: every lane reaches the warp
-  // collectives of dense_set_bits
   for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x; b < n; b += stride) {
     const uint64_t i = b + threadIdx.x;
     const bool keep = i < n;

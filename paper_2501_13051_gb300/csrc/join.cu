@@ -26,6 +26,7 @@ namespace {
 constexpr int kCT = 256;  // count pass: threads; tiles of kScanTile rows
 constexpr int kCItems = kScanTile / kCT;
 constexpr int kJT = 256;  // write pass threads
+constexpr int kDU = 4;    // write pass into a bitmap: outputs per thread in flight
 constexpr int kJItems = 8;
 constexpr int kJTile = kJT * kJItems;  // merged items per block
 
@@ -180,38 +181,62 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
     s_start[r] = st;
   }
   __syncthreads();
+  // output o's head values; false when a filter drops it
+  auto tuple_at = [&](uint64_t o, uint32_t (&vals)[kMaxK]) -> bool {
+    uint32_t lo = 0, hi = nrows;  // largest r with s_off[r] <= o
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_off[mid] <= o)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const uint64_t row = r_lo + lo;
+    const uint64_t brow = (uint64_t)s_start[lo] + (o - s_off[lo]);
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k)
+      if (k < (int)j.out_k) vals[k] = ref_value(j, probe, j.out[k], row, brow);
+    bool keep = true;
+    if (FILTER) {
+      for (uint32_t q = 0; q < j.n_eq; ++q)
+        keep &= ref_value(j, probe, j.eq[q][0], row, brow) ==
+                ref_value(j, probe, j.eq[q][1], row, brow);
+      for (uint32_t q = 0; q < j.n_neq; ++q)
+        keep &= ref_value(j, probe, j.neq[q][0], row, brow) !=
+                ref_value(j, probe, j.neq[q][1], row, brow);
+    }
+    return keep;
+  };
+  if (DENSE) {
+    // kDU outputs per thread at a time, each stage's loads all in flight:
+    // the gathers, the words' reads, the atomics of missing bits
+    bool bad = false;
+    for (uint64_t ob = o0; ob < o1; ob += (uint64_t)kJT * kDU) {
+      uint32_t word[kDU], bit[kDU];
+      bool need[kDU];
+#pragma unroll
+      for (int u = 0; u < kDU; ++u) {
+        const uint64_t o = ob + (uint64_t)u * kJT + threadIdx.x;
+        uint32_t vals[kMaxK] = {0, 0, 0, 0};
+        word[u] = bit[u] = 0;
+        need[u] = o < o1 && tuple_at(o, vals);
+        if (need[u] && !dense_locate(dset, vals, &word[u], &bit[u])) bad = true, need[u] = false;
+      }
+#pragma unroll
+      for (int u = 0; u < kDU; ++u)
+        if (need[u]) need[u] = dense_missing(dset, word[u], bit[u]);
+#pragma unroll
+      for (int u = 0; u < kDU; ++u)
+        if (need[u]) atomicOr(dset.words + word[u], bit[u]);
+    }
+    if (bad && err) atomicOr(err, kErrCapacity);
+    return;
+  }
   for (uint64_t ob = o0; ob < o1; ob += kJT) {
     const uint64_t o = ob + threadIdx.x;
     const bool valid = o < o1;
     uint32_t vals[kMaxK] = {0, 0, 0, 0};
-    bool keep = valid;
-    if (valid) {
-      uint32_t lo = 0, hi = nrows;  // largest r with s_off[r] <= o
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (s_off[mid] <= o)
-          lo = mid;
-        else
-          hi = mid;
-      }
-      const uint64_t row = r_lo + lo;
-      const uint64_t brow = (uint64_t)s_start[lo] + (o - s_off[lo]);
-#pragma unroll
-      for (int k = 0; k < kMaxK; ++k)
-        if (k < (int)j.out_k) vals[k] = ref_value(j, probe, j.out[k], row, brow);
-      if (FILTER) {
-        for (uint32_t q = 0; q < j.n_eq; ++q)
-          keep &= ref_value(j, probe, j.eq[q][0], row, brow) ==
-                  ref_value(j, probe, j.eq[q][1], row, brow);
-        for (uint32_t q = 0; q < j.n_neq; ++q)
-          keep &= ref_value(j, probe, j.neq[q][0], row, brow) !=
-                  ref_value(j, probe, j.neq[q][1], row, brow);
-      }
-    }
-    if (DENSE) {  // the loop's trip count is the block's: every lane is here
-      dense_set_bits(dset, vals, keep, err);
-      continue;
-    }
+    const bool keep = valid && tuple_at(o, vals);
     uint64_t pos;
     if (FILTER) {
       uint32_t cnt;
