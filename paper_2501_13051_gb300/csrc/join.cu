@@ -27,6 +27,7 @@ constexpr int kCT = 256;  // count pass: threads; tiles of kScanTile rows
 constexpr int kCItems = kScanTile / kCT;
 constexpr int kJT = 256;  // write pass threads
 constexpr int kDU = 4;    // write pass into a bitmap: outputs per thread in flight
+constexpr uint32_t kDRows = 8;  // ... and the most probe rows a block walks one by one
 constexpr int kJItems = 8;
 constexpr int kJTile = kJT * kJItems;  // merged items per block
 
@@ -181,18 +182,9 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
     s_start[r] = st;
   }
   __syncthreads();
-  // output o's head values; false when a filter drops it
-  auto tuple_at = [&](uint64_t o, uint32_t (&vals)[kMaxK]) -> bool {
-    uint32_t lo = 0, hi = nrows;  // largest r with s_off[r] <= o
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (s_off[mid] <= o)
-        lo = mid;
-      else
-        hi = mid;
-    }
-    const uint64_t row = r_lo + lo;
-    const uint64_t brow = (uint64_t)s_start[lo] + (o - s_off[lo]);
+  // head values of probe row `row` matched with build row `brow`; false
+  // when a filter drops the pair
+  auto tuple_of = [&](uint64_t row, uint64_t brow, uint32_t (&vals)[kMaxK]) -> bool {
 #pragma unroll
     for (int k = 0; k < kMaxK; ++k)
       if (k < (int)j.out_k) vals[k] = ref_value(j, probe, j.out[k], row, brow);
@@ -207,6 +199,41 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
     }
     return keep;
   };
+  // output o of the block: its probe row found in the staged offsets
+  auto tuple_at = [&](uint64_t o, uint32_t (&vals)[kMaxK]) -> bool {
+    uint32_t lo = 0, hi = nrows;  // largest r with s_off[r] <= o
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_off[mid] <= o)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    return tuple_of(r_lo + lo, (uint64_t)s_start[lo] + (o - s_off[lo]), vals);
+  };
+  if (DENSE && nrows <= kDRows) {
+    // a few probe rows with long ranges (the hot keys): the block walks
+    // each row's outputs in turn, with no search for the row
+    bool bad = false;
+    for (uint32_t r = 0; r < nrows; ++r) {
+      const uint64_t ra = s_off[r];
+      const uint64_t a = ra > o0 ? ra : o0;
+      const uint64_t e = r + 1 < nrows ? s_off[r + 1] : o1;
+      const uint64_t b = e < o1 ? e : o1;
+      for (uint64_t o = a + threadIdx.x; o < b; o += kJT) {
+        uint32_t vals[kMaxK] = {0, 0, 0, 0};
+        if (!tuple_of(r_lo + r, (uint64_t)s_start[r] + (o - ra), vals)) continue;
+        uint32_t word, bit;
+        if (!dense_locate(dset, vals, &word, &bit)) {
+          bad = true;
+          continue;
+        }
+        if (dense_missing(dset, word, bit)) atomicOr(dset.words + word, bit);
+      }
+    }
+    if (bad && err) atomicOr(err, kErrCapacity);
+    return;
+  }
   if (DENSE) {
     // kDU outputs per thread at a time, each stage's loads all in flight:
     // the gathers, the words' reads, the atomics of missing bits

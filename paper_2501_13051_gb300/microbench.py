@@ -13,6 +13,11 @@ sorted new pairs, half of them already in full), scan (n counts).  Inputs
 exceed the 129 MB L2 for n >= 2^24, and each timed repeat is preceded by an
 L2-sized write.  Used for the ncu captures of single kernels.
 
+--fixpoint NAME runs whole fixpoints of one of the benchmark programs in the
+engine's default form (sg-200k, tc-1000, points-to at scale 2^-9,
+owl-20m), --repeat times, one JSON line each: the command the ncu captures
+of a kernel inside a fixpoint run.
+
 --dist zipf draws the keys Zipf(1.1) over the same domain (the join's probe
 keys against unique build keys, so the output stays n rows).  --sweep runs
 every step at 2^24, 2^26 and 2^28 (diff_merge and the Zipf cases up to
@@ -105,15 +110,55 @@ def time_case(run, repeat, flush):
     return float(np.median(times))
 
 
+FIXPOINTS = {
+    "sg-200k": lambda W: W.sg_program(W.random_forest(200_000, 2)),
+    "tc-1000": lambda W: W.tc_program(W.er_graph(1000, 1500, 1)),
+    "points-to": lambda W: W.points_to_program(W.points_to_edb(1 / 512, 3)),
+    "owl-20m": lambda W: W.owl_program(*W.owl_triples(20_000_000, 4)),
+}
+
+
+def run_fixpoints(name, repeat):
+    import time
+
+    import torch
+
+    from . import cdl
+    from . import workloads as W
+
+    prog = FIXPOINTS[name](W)
+    dev = {nm: [torch.from_numpy(np.ascontiguousarray(r[:, k]).view(np.int32)).cuda()
+                for k in range(prog.arity[nm])] for nm, r in prog.edb.items()}
+    for i in range(repeat):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        with cdl.Engine() as e:
+            for nm, ar in prog.arity.items():
+                e.relation(nm, ar)
+            for nm, cols in dev.items():
+                e.load(nm, cols)
+            for r in prog.rules:
+                e.rule(r.head, r.body, r.neq)
+            st = e.run()
+        torch.cuda.synchronize()
+        print(json.dumps({"fixpoint": name, "run": i, "ms": (time.perf_counter() - t) * 1e3,
+                          "iterations": st.iterations, "derived": st.derived_tuples,
+                          "kernel_launches": st.kernel_launches}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--step", choices=["hash", "join", "sort", "diff_merge", "scan"])
+    ap.add_argument("--fixpoint", choices=sorted(FIXPOINTS))
     ap.add_argument("--n", type=int, default=1 << 24)
     ap.add_argument("--repeat", type=int, default=5)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "zipf"])
     ap.add_argument("--sweep", action="store_true")
     args = ap.parse_args()
+    if args.fixpoint:
+        run_fixpoints(args.fixpoint, args.repeat)
+        return
 
     import torch
 
