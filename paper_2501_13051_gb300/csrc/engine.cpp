@@ -362,6 +362,8 @@ struct cdl_engine {
   static constexpr double kDirectMaxTuples = double(1 << 24);
   static constexpr uint64_t kPredictMinRows = 1 << 15;  // smaller probes keep the count pass
   static constexpr int kDenseBits = 28;  // default bound of a dense relation's tuple space (32 MB)
+  static constexpr uint64_t kGroupRows = 1 << 21;  // larger new-tuple sets sort on their own
+  static constexpr size_t kGroupMin = 4;           // fewer relations sort one by one
   struct Deferred {
     std::tuple<size_t, size_t, size_t> step;
     uint32_t head = 0;  // relation the join appends to
@@ -1477,6 +1479,61 @@ struct cdl_engine {
     }
   }
 
+  // A round's new tuples of several relations of one arity, each at most
+  // kGroupRows, are sorted as one (as grouped loads are): a leading column
+  // numbers the relation, so one sort replaces one per relation, and each
+  // relation's rows come out as a contiguous, sorted segment whose bounds
+  // are the known row counts.  rows[i] then views relation i's segment in
+  // one of bufs.
+  cdl_status sort_groups(std::vector<DCols>& bufs, std::vector<DCols>& rows,
+                         std::vector<uint8_t>& grouped) {
+    for (uint32_t k = 1; k < (uint32_t)kMaxK; ++k) {
+      std::vector<uint32_t> grp;
+      for (uint32_t i = 0; i < rels.size(); ++i) {
+        const Relation& R = *rels[i];
+        const uint64_t n = h_ctl[kSlotCursor + i];
+        if (R.idb && !R.dset.words && R.arity == k && n > 0 && n <= kGroupRows &&
+            n <= R.fresh.cap && R.full.n + n <= 0xFFFFFFFFull)
+          grp.push_back(i);
+      }
+      if (grp.size() < kGroupMin) continue;
+      const uint32_t ng = (uint32_t)grp.size();
+      std::vector<uint64_t> off{0};
+      std::vector<ColsIn> src;
+      uint32_t bits[kMaxK] = {bits_of(ng - 1), 0, 0, 0};
+      for (uint32_t i : grp) {
+        const Relation& R = *rels[i];
+        off.push_back(off.back() + h_ctl[kSlotCursor + i]);
+        src.push_back(R.fresh.in());
+        for (uint32_t c = 0; c < k; ++c) bits[c + 1] = std::max(bits[c + 1], bits_of(R.bound[c]));
+      }
+      DCols comb;
+      DBuf dsrc = alloc(sizeof(ColsIn) * ng), doff = alloc(8 * off.size());
+      if (!alloc_cols(comb, k + 1, off.back()) || !dsrc.p || !doff.p)
+        return fail(CDL_E_NOMEM, "grouped sort");
+      comb.n = off.back();
+      cudaError_t e = cudaMemcpyAsync(dsrc.p, src.data(), sizeof(ColsIn) * ng,
+                                      cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(doff.p, off.data(), 8 * off.size(), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = concat_segments(ctx, comb.out(), static_cast<const ColsIn*>(dsrc.p), k,
+                            static_cast<const uint64_t*>(doff.p), ng, comb.n);
+      if (e != cudaSuccess) return cuda_fail(e, "grouped sort");
+      cdl_status r = sort_cols(comb, bits);
+      if (r != CDL_OK) return r;
+      for (uint32_t g = 0; g < ng; ++g) {
+        DCols& v = rows[grp[g]];
+        v.k = k;
+        v.n = v.cap = off[g + 1] - off[g];
+        for (uint32_t c = 0; c < k; ++c) v.c[c] = comb.c[c + 1] + off[g];
+        grouped[grp[g]] = 1;
+      }
+      bufs.push_back(std::move(comb));
+    }
+    return CDL_OK;
+  }
+
   // Dense relations at a round's end: the rows written to fresh (copies,
   // single-pass joins) set their bits too, then the bits come out as the
   // round's sorted unique new rows, whose numbers are read back at once.
@@ -1953,6 +2010,11 @@ struct cdl_engine {
       recording = false;
       if (status == CDL_OK) status = extract_dense();
       if (status != CDL_OK) break;
+      // relations of one arity with few new tuples each are sorted as one
+      std::vector<DCols> group_bufs, sorted_rows(nr);
+      std::vector<uint8_t> grouped(nr, 0);
+      if (!opt.n_instances) status = sort_groups(group_bufs, sorted_rows, grouped);
+      if (status != CDL_OK) break;
       std::vector<uint8_t> merged(nr, 0);
       for (uint32_t i = 0; i < nr; ++i) {
         Relation& R = *rels[i];
@@ -1982,6 +2044,12 @@ struct cdl_engine {
         if (R.full.n + R.fresh.n > 0xFFFFFFFFull) {
           status = fail(CDL_E_CAPACITY, "relation " + R.name + " would exceed 2^32 tuples");
           break;
+        }
+        if (grouped[i]) {  // sorted with its group: a segment of the group's rows
+          status = merge_into(R, sorted_rows[i], &R.delta, kSlotDelta + i);
+          if (status != CDL_OK) break;
+          merged[i] = 1;
+          continue;
         }
         uint32_t bits[kMaxK];
         for (uint32_t k = 0; k < R.arity; ++k) bits[k] = bits_of(R.bound[k]);

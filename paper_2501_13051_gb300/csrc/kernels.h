@@ -266,6 +266,12 @@ cudaError_t round_end(Ctx& c, GraphRel* cur, GraphRel* next, uint32_t nrel, Grap
 // nseg + 1 device entries and off[nseg] = total.
 cudaError_t fill_segments(Ctx& c, uint32_t* col, const uint64_t* off, uint32_t nseg,
                           uint64_t total);
+// Segments side by side behind a leading column of segment numbers: row j
+// of segment s (rows [off[s], off[s + 1]), off and src in device memory)
+// gets out.c[0][j] = s and out.c[1 + c][j] = src[s].c[c][j - off[s]],
+// c < k <= 3.
+cudaError_t concat_segments(Ctx& c, ColsOut out, const ColsIn* src, uint32_t k,
+                            const uint64_t* off, uint32_t nseg, uint64_t total);
 // bounds[i] (i = 0..n_instances) = first row of the sorted column inst whose
 // value is >= i: instance i occupies rows [bounds[i], bounds[i + 1]).
 cudaError_t instance_bounds(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,

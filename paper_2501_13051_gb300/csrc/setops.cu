@@ -177,6 +177,39 @@ cudaError_t fill_segments(Ctx& c, uint32_t* col, const uint64_t* off, uint32_t n
   return cudaGetLastError();
 }
 
+// Row j of segment s (rows [off[s], off[s + 1])): out.c[0][j] = s and
+// out.c[1 + c][j] = column c of src[s] at row j - off[s].
+__global__ void k_concat_segments(ColsOut out, const ColsIn* __restrict__ src, uint32_t k,
+                                  const uint64_t* __restrict__ off, uint32_t nseg,
+                                  uint64_t total) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total;
+       j += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = nseg;  // the last segment starting at or before j
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(off + mid) <= j)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const uint64_t r = j - __ldg(off + lo);
+    out.c[0][j] = lo;
+#pragma unroll
+    for (uint32_t c = 0; c + 1 < (uint32_t)kMaxK; ++c)
+      if (c < k) out.c[c + 1][j] = __ldg(src[lo].c[c] + r);
+  }
+}
+
+cudaError_t concat_segments(Ctx& c, ColsOut out, const ColsIn* src, uint32_t k,
+                            const uint64_t* off, uint32_t nseg, uint64_t total) {
+  if (total == 0 || nseg == 0) return cudaSuccess;
+  ProfScope p(c, kMisc, (8.0 * k + 4.0) * total);
+  uint64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_concat_segments<<<(unsigned)blocks, 256, 0, c.st>>>(out, src, k, off, nseg, total);
+  return cudaGetLastError();
+}
+
 cudaError_t instance_bounds(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_instances,
                             uint64_t* bounds) {
   ProfScope p(c, kRetire, 8.0 * (n_instances + 1));

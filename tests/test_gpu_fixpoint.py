@@ -70,6 +70,34 @@ def test_owl_scaled(cdl, oracle_lib):
     check(cdl, oracle_lib, W.owl_program(*W.owl_triples(200_000, 4, n_entities=50_000)))
 
 
+def many_relations_program(seed):
+    """Six derived relations of arity 2, five of arity 1 and four of arity 3
+    (independent closures over small random graphs, with a constant head
+    column): a round's new tuples of each arity are sorted as one group."""
+    arity, edb, rules = {}, {}, []
+    for i in range(6):
+        edb[f"e{i}"] = W.er_graph(300, 420, seed + i)
+        arity[f"e{i}"] = arity[f"p{i}"] = 2
+        rules += [W.Rule((f"p{i}", ("x", "y")), ((f"e{i}", ("x", "y")),)),
+                  W.Rule((f"p{i}", ("x", "z")), ((f"p{i}", ("x", "y")), (f"e{i}", ("y", "z"))))]
+    for i in range(5):
+        arity[f"r{i}"] = 1
+        rules += [W.Rule((f"r{i}", ("y",)), ((f"e{i}", (i, "y")),)),
+                  W.Rule((f"r{i}", ("y",)), ((f"r{i}", ("x",)), (f"e{i}", ("x", "y"))))]
+    for i in range(4):
+        arity[f"t{i}"] = 3
+        rules += [W.Rule((f"t{i}", ("x", "y", 7 + i)), ((f"e{i}", ("x", "y")),)),
+                  W.Rule((f"t{i}", ("x", "z", "c")),
+                         ((f"t{i}", ("x", "y", "c")), (f"e{i}", ("y", "z"))))]
+    return W.Program(arity, rules, edb)
+
+
+@FORMS
+@pytest.mark.parametrize("seed", [1, 2])
+def test_relations_sorted_as_groups(cdl, oracle_lib, seed, dense):
+    check(cdl, oracle_lib, many_relations_program(seed), dense_bits=dense)
+
+
 @FORMS
 @pytest.mark.parametrize("seed", range(40))
 def test_random_programs(cdl, oracle_lib, seed, dense):
