@@ -326,8 +326,7 @@ def bench_gb300(args, rank, world, dist):
         for _ in range(6):
             with cdl.Engine(n_instances=ninst, autotune=2, tune_cache=cache) as e:
                 declare(e)
-                for nm, cols in dev_edb.items():
-                    e.load(nm, cols)
+                e.load_many(dev_edb)  # one check of every relation's values
                 rules(e)
                 e.run()
         form.update(autotune=1, tune_cache=cache)
@@ -343,8 +342,7 @@ def bench_gb300(args, rank, world, dist):
     def step(timing, plain=False):
         with cdl.Engine(timing=timing, n_instances=ninst, **({} if plain else form)) as e:
             declare(e)
-            for nm, cols in dev_edb.items():
-                e.load(nm, cols)
+            e.load_many(dev_edb)  # one check of every relation's values
             rules(e)
             st = e.run()
             return st, (e.kernel_profile() if timing else None)
@@ -418,8 +416,7 @@ def bench_gb300(args, rank, world, dist):
     sizes = {}
     with cdl.Engine(n_instances=ninst, **form) as e:
         declare(e)
-        for nm, cols in dev_edb.items():
-            e.load(nm, cols)
+        e.load_many(dev_edb)  # one check of every relation's values
         rules(e)
         e.run()
         sizes = {nm: e.size(nm) for nm in idb}
@@ -429,8 +426,7 @@ def bench_gb300(args, rank, world, dist):
     def step_e2e():
         with cdl.Engine(n_instances=ninst, **form) as e:
             declare(e)
-            for nm, cols in pinned_in.items():
-                e.load(nm, cols)
+            e.load_many(pinned_in)  # one check of every relation's values
             rules(e)
             s = e.run()
             for nm in idb:

@@ -149,6 +149,16 @@ cdl_status cdl_relation_create(cdl_engine* e, const char* name, uint32_t arity, 
 cdl_status cdl_relation_load(cdl_engine* e, cdl_rel rel, const uint32_t* const* cols,
                              uint64_t n, int on_device);
 
+/* Loads several relations at once: the same as count calls
+ * cdl_relation_load(e, rels[i], cols[i], n[i], on_device), except that the
+ * values of all of them are checked together with one wait for the device.
+ * Returns CDL_E_VALUE if any of them holds 0xFFFFFFFF, and then none of them
+ * is added.  CDL_E_INVALID (nothing added) for a null array, an unknown
+ * relation or a null column pointer. */
+cdl_status cdl_relations_load(cdl_engine* e, uint32_t count, const cdl_rel* rels,
+                              const uint32_t* const* const* cols, const uint64_t* n,
+                              int on_device);
+
 typedef struct {
   uint32_t is_const; /* 0: variable, 1: constant */
   uint32_t v;        /* variable id (any small integer) or constant value */

@@ -108,6 +108,7 @@ def lib():
         "cdl_destroy": (ctypes.c_int, [VP]),
         "cdl_relation_create": (ctypes.c_int, [VP, ctypes.c_char_p, U32, P(U32)]),
         "cdl_relation_load": (ctypes.c_int, [VP, U32, PP, U64, ctypes.c_int]),
+        "cdl_relations_load": (ctypes.c_int, [VP, U32, P(U32), P(PP), P(U64), ctypes.c_int]),
         "cdl_rule_add": (ctypes.c_int, [VP, P(RuleS)]),
         "cdl_run": (ctypes.c_int, [VP, P(Stats)]),
         "cdl_relation_size": (ctypes.c_int, [VP, U32, P(U64)]),
@@ -304,25 +305,42 @@ class Engine:
         self.arity[name] = arity
         return out.value
 
+    def _columns(self, name, rows):
+        """(column pointers, n, on_device, objects to keep alive) of one load."""
+        ar = self.arity[name]
+        if isinstance(rows, (list, tuple)):
+            cols = list(rows)
+            n = cols[0].numel() if cols else 0
+            return _ptrs(cols), n, 1 if (cols and cols[0].is_cuda) else 0, cols
+        a = np.ascontiguousarray(np.asarray(rows, dtype=np.uint32).reshape(-1, ar))
+        keep = [np.ascontiguousarray(a[:, k]) for k in range(ar)]
+        return _ptrs([c.ctypes.data for c in keep]), a.shape[0], 0, keep
+
     def load(self, name: str, rows) -> None:
         """rows: (n, arity) host array of uint32, or a list of `arity` int32 /
         uint32 column tensors (CUDA tensors are read on the device, CPU
         tensors -- e.g. pinned -- are copied from host memory)."""
-        rel, ar = self.rels[name], self.arity[name]
-        if isinstance(rows, (list, tuple)):
-            cols = list(rows)
-            n = cols[0].numel() if cols else 0
-            keep = cols
-            on_dev = 1 if (cols and cols[0].is_cuda) else 0
-        else:
-            a = np.ascontiguousarray(np.asarray(rows, dtype=np.uint32).reshape(-1, ar))
-            n = a.shape[0]
-            keep = [np.ascontiguousarray(a[:, k]) for k in range(ar)]
-            cols = [c.ctypes.data for c in keep]
-            on_dev = 0
-        arr = _ptrs(cols)
-        self._check(self._L.cdl_relation_load(self._h, rel, arr, n, on_dev))
+        arr, n, on_dev, keep = self._columns(name, rows)
+        self._check(self._L.cdl_relation_load(self._h, self.rels[name], arr, n, on_dev))
         del keep
+
+    def load_many(self, relations: dict) -> None:
+        """{name: rows} (as for load, all on the device or all in host
+        memory) in one call: one check of all values, all added or none."""
+        names = list(relations)
+        if not names:
+            return
+        parts = [self._columns(nm, relations[nm]) for nm in names]
+        on_dev = {p[2] for p in parts if p[1]}
+        if len(on_dev) > 1:
+            raise ValueError("load_many: mix of device and host columns")
+        rel = (ctypes.c_uint32 * len(names))(*[self.rels[nm] for nm in names])
+        cols = (ctypes.POINTER(ctypes.c_void_p) * len(names))(
+            *[ctypes.cast(p[0], ctypes.POINTER(ctypes.c_void_p)) for p in parts])
+        ns = (ctypes.c_uint64 * len(names))(*[p[1] for p in parts])
+        self._check(self._L.cdl_relations_load(self._h, len(names), rel, cols, ns,
+                                               on_dev.pop() if on_dev else 0))
+        del parts
 
     def rule(self, head, body, neq=()) -> None:
         var_id = {}
@@ -353,8 +371,7 @@ class Engine:
     def load_program(self, program) -> None:
         for name, ar in program.arity.items():
             self.relation(name, ar)
-        for name, rows in program.edb.items():
-            self.load(name, rows)
+        self.load_many(dict(program.edb))
         for r in program.rules:
             self.rule(r.head, r.body, r.neq)
 

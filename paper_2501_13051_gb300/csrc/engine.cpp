@@ -2294,6 +2294,53 @@ struct cdl_engine {
     return CDL_OK;
   }
 
+  // Several loads with one check: every load's columns are copied and
+  // scanned (maxima per column, the reserved value) back to back, then one
+  // wait reads all maxima and the error word.  All are added, or none.
+  cdl_status load_many(uint32_t count, const cdl_rel* rl, const uint32_t* const* const* cols,
+                       const uint64_t* ns, int on_device) {
+    if (ran) return fail(CDL_E_STATE, "loads must precede cdl_run");
+    for (uint32_t i = 0; i < count; ++i) {
+      if (rl[i] >= rels.size()) return fail(CDL_E_INVALID, "no such relation");
+      if (ns[i] > 0xFFFFFFFFull) return fail(CDL_E_CAPACITY, "load exceeds 2^32 tuples");
+      if (!ns[i]) continue;
+      if (!cols[i]) return fail(CDL_E_INVALID, "null column pointer");
+      for (uint32_t k = 0; k < rels[rl[i]]->arity; ++k)
+        if (!cols[i][k]) return fail(CDL_E_INVALID, "null column pointer");
+    }
+    DBuf mx = alloc(4 * kMaxK * std::max<uint32_t>(count, 1));
+    if (!mx.p) return fail(CDL_E_NOMEM, "load maxima");
+    std::vector<DCols> in(count);
+    for (uint32_t i = 0; i < count; ++i) {
+      if (!ns[i]) continue;
+      const uint32_t ar = rels[rl[i]]->arity;
+      if (!alloc_cols(in[i], ar, ns[i])) return fail(CDL_E_NOMEM, "load buffer");
+      in[i].n = ns[i];
+      cudaError_t e = cudaSuccess;
+      for (uint32_t k = 0; k < ar && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(in[i].c[k], cols[i][k], ns[i] * 4,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = check_values(ctx, in[i].in(), ar, ns[i], static_cast<uint32_t*>(mx.p) + kMaxK * i);
+      if (e != cudaSuccess) return cuda_fail(e, "load");
+    }
+    std::vector<uint32_t> hmx(kMaxK * std::max<uint32_t>(count, 1));
+    cudaError_t e = cudaMemcpyAsync(hmx.data(), mx.p, 4 * hmx.size(), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "load maxima");
+    cdl_status r = fetch(kSlotScratch, 1);
+    if (r != CDL_OK) {
+      cudaMemsetAsync(dslot(kSlotErr), 0, 8, st);
+      return r;
+    }
+    for (uint32_t i = 0; i < count; ++i) {
+      if (!ns[i]) continue;
+      Relation& R = *rels[rl[i]];
+      for (uint32_t k = 0; k < R.arity; ++k) R.bound[k] = std::max(R.bound[k], hmx[kMaxK * i + k]);
+      R.pending.push_back(std::move(in[i]));
+    }
+    return CDL_OK;
+  }
+
   // Sorts every relation's checked loads and merges them into its full
   // version (repeats dropped), all relations back to back with one read-back
   // of the sizes at the end.
@@ -2492,6 +2539,13 @@ cdl_status cdl_relation_load(cdl_engine* e, cdl_rel rel, const uint32_t* const* 
   if (!e || (!cols && n)) return CDL_E_INVALID;
   if (rel >= e->rels.size()) return e->fail(CDL_E_INVALID, "no such relation");
   return e->load(rel, cols, n, on_device);
+}
+
+cdl_status cdl_relations_load(cdl_engine* e, uint32_t count, const cdl_rel* rels,
+                              const uint32_t* const* const* cols, const uint64_t* n,
+                              int on_device) {
+  if (!e || (count && (!rels || !cols || !n))) return CDL_E_INVALID;
+  return e->load_many(count, rels, cols, n, on_device);
 }
 
 cdl_status cdl_rule_add(cdl_engine* e, const cdl_rule* rule) {

@@ -135,8 +135,7 @@ def run_fixpoints(name, repeat):
         with cdl.Engine() as e:
             for nm, ar in prog.arity.items():
                 e.relation(nm, ar)
-            for nm, cols in dev.items():
-                e.load(nm, cols)
+            e.load_many(dev)
             for r in prog.rules:
                 e.rule(r.head, r.body, r.neq)
             st = e.run()

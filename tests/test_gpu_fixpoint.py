@@ -145,6 +145,26 @@ def test_reserved_value_rejected(cdl):
         assert eng.size("r") == 1
 
 
+def test_load_many_is_all_or_nothing(cdl):
+    import torch
+    good = np.array([[1, 2], [3, 4], [1, 2]], np.uint32)
+    bad = np.array([[5, 6], [7, 0xFFFFFFFF]], np.uint32)
+    with cdl.Engine() as eng:
+        for nm in ("a", "b", "c"):
+            eng.relation(nm, 2)
+        with pytest.raises(cdl.CdlError) as ei:
+            eng.load_many({"a": good, "b": bad})
+        assert ei.value.name == "CDL_E_VALUE"
+        assert eng.size("a") == 0 and eng.size("b") == 0  # neither was added
+        dev = [torch.from_numpy(np.ascontiguousarray(good[:, k]).view(np.int32)).cuda()
+               for k in range(2)]
+        eng.load_many({"a": good, "c": np.zeros((0, 2), np.uint32)})
+        eng.load_many({"b": dev})
+        assert eng.size("a") == 2 and eng.size("b") == 2 and eng.size("c") == 0
+        with pytest.raises(ValueError):
+            eng.load_many({"a": good, "b": dev})  # host and device columns in one call
+
+
 def test_max_iters(cdl):
     prog = W.tc_program(W.er_graph(100, 200, 1))
     with pytest.raises(cdl.CdlError) as ei:
