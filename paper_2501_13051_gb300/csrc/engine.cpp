@@ -349,6 +349,16 @@ struct cdl_engine {
   // learned join-size estimator
   DBuf est_w, est_wb, est_io;  // FP32 and BF16 parameters; features + prediction
   float* h_est = nullptr;      // pinned host mirror of est_io
+  // A round's predictions for its first joins that write a head relation,
+  // computed together: a planning pass over the rules launches their
+  // features (est_plan), one inference and one read-back follow, and the
+  // joins then run without a wait each.
+  static constexpr uint32_t kEstBatch = 1024;
+  DBuf est_bio;              // kEstBatch x kMlpIn features, then kEstBatch predictions
+  float* h_batch = nullptr;  // pinned host mirror of est_bio
+  bool est_plan = false;
+  uint32_t est_nb = 0;
+  std::map<std::tuple<size_t, size_t, size_t>, uint32_t> est_slot;
   bool est_weights = false;
   double est_margin = 1.0;  // the configured margin (log2 units)
   double est_boost = 0.0;   // added after each overrun of this run, up to 4
@@ -506,6 +516,7 @@ struct cdl_engine {
     pool.release_all();
     if (h_ctl) cudaFreeHost(h_ctl);
     if (h_est) cudaFreeHost(h_est);
+    if (h_batch) cudaFreeHost(h_batch);
   }
 
   cdl_status fail(cdl_status s, const std::string& m) {
@@ -878,7 +889,10 @@ struct cdl_engine {
       if (atoms[i].n == 0) return CDL_OK;  // joins with an empty table derive nothing
       if (!atoms[i].vars.empty()) chain.push_back(i);
     }
-    if (chain.size() <= 1) return emit_from(rule, chain.empty() ? nullptr : &atoms[chain[0]], atoms[0]);
+    if (chain.size() <= 1) {
+      if (est_plan) return CDL_OK;
+      return emit_from(rule, chain.empty() ? nullptr : &atoms[chain[0]], atoms[0]);
+    }
     if (std::find(chain.begin(), chain.end(), start) == chain.end()) start = chain[0];
     const size_t nb = chain.size();
     std::vector<size_t> order{start};
@@ -1016,12 +1030,35 @@ struct cdl_engine {
                            !(last && rels[rule.head.rel]->dset.words) &&
                            P.n >= (opt.est_min_rows ? opt.est_min_rows : kPredictMinRows);
       const bool feats = ix != nullptr && (predict || opt.estimator >= 2);
-      if (feats) {
+      auto features = [&]() {
         const Relation* PR = P.rel >= 0 ? rels[P.rel].get() : nullptr;
         const auto po = prev_out.find(step_key);
-        JoinFeatureHost hf{(float)(PR ? PR->full.n : P.n), (float)ix->distinct, (float)cur_round,
-                           po == prev_out.end() ? 0.f : (float)po->second,
-                           (float)rels[rule.head.rel]->delta.n, filter ? 1.f : 0.f};
+        return JoinFeatureHost{(float)(PR ? PR->full.n : P.n), (float)ix->distinct,
+                               (float)cur_round, po == prev_out.end() ? 0.f : (float)po->second,
+                               (float)rels[rule.head.rel]->delta.n, filter ? 1.f : 0.f};
+      };
+      if (est_plan) {  // planning pass: the features of a first join that writes a head
+        if (predict && last && t == 1 && est_nb < kEstBatch) {
+          float* X = static_cast<float*>(est_bio.p) + (size_t)est_nb * kMlpIn;
+          cudaError_t e = join_features(ctx, P.c[js.pk0], js.pk1 == 0xFFu ? nullptr : P.c[js.pk1],
+                                        P.n, ix->cols[hkey[0]],
+                                        hkey.size() > 1 ? ix->cols[hkey[1]] : nullptr, B.n,
+                                        features(), X);
+          if (e != cudaSuccess) return cuda_fail(e, "join features");
+          est_slot[step_key] = est_nb++;
+        }
+        return CDL_OK;
+      }
+      // predicted in the round's batch: no launch, no wait here
+      const auto bslot = est_slot.find(step_key);
+      const bool batched = predict && last && bslot != est_slot.end() &&
+                           deferred.size() < kMaxDeferred;
+      if (feats && batched) {
+        std::copy(h_batch + (size_t)bslot->second * kMlpIn,
+                  h_batch + (size_t)(bslot->second + 1) * kMlpIn, h_est);
+        h_est[kMlpIn] = h_batch[(size_t)kEstBatch * kMlpIn + bslot->second];
+      } else if (feats) {
+        const JoinFeatureHost hf = features();
         float* io = static_cast<float*>(est_io.p);
         cudaError_t e = join_features(ctx, P.c[js.pk0], js.pk1 == 0xFFu ? nullptr : P.c[js.pk1],
                                       P.n, ix->cols[hkey[0]],
@@ -1040,10 +1077,13 @@ struct cdl_engine {
       };
       bool predicted = false;
       if (predict) {
-        // single pass into a buffer sized by the prediction
-        r = fetch(kSlotScratch, kSlotCursor + (uint32_t)rels.size() - kSlotScratch);
-        if (r != CDL_OK) return r;
-        note_cursors();
+        // single pass into a buffer sized by the prediction; a batched one
+        // sizes it from the host's bound on the cursor instead of reading it
+        if (!batched) {
+          r = fetch(kSlotScratch, kSlotCursor + (uint32_t)rels.size() - kSlotScratch);
+          if (r != CDL_OK) return r;
+          note_cursors();
+        }
         if (last && rels[rule.head.rel]->fresh_overflow) return CDL_OK;  // redone exact
         const double want =
             std::exp2(std::min(40.0, (double)h_est[kMlpIn] + est_margin + est_boost));
@@ -1052,7 +1092,9 @@ struct cdl_engine {
         if (want <= kDirectMaxTuples) {
           const uint64_t cap = std::max<uint64_t>(256, (uint64_t)std::ceil(want));
           Relation* H = last ? rels[rule.head.rel].get() : nullptr;
-          const uint64_t cur0 = last ? h_ctl[kSlotCursor + rule.head.rel] : 0;
+          const uint64_t cur0 = !last ? 0
+                                : batched ? H->fresh_ub
+                                          : h_ctl[kSlotCursor + rule.head.rel];
           uint64_t* cursor = dslot(last ? kSlotCursor + rule.head.rel : kSlotAux);
           bool room = true;
           ColsOut out{};
@@ -1112,8 +1154,10 @@ struct cdl_engine {
             }
           }
           // the prediction was too small: undo the claims, then the exact join
+          // (a batched one claimed nothing: it always takes the path above
+          // when its buffer has room)
           ++est_over;
-          if (last) {
+          if (last && !batched) {
             h_ctl[kSlotScratch] = cur0;
             cudaError_t e = cudaMemcpyAsync(cursor, h_ctl + kSlotScratch, 8, cudaMemcpyHostToDevice, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1210,7 +1254,23 @@ struct cdl_engine {
     return CDL_OK;
   }
 
+  // A body atom that reads its relation's columns as they are (distinct
+  // variables only): its source needs no selection kernel.
+  static bool plain_atom(const AtomR& a) {
+    for (size_t i = 0; i < a.t.size(); ++i) {
+      if (a.t[i].is_const) return false;
+      for (size_t j = 0; j < i; ++j)
+        if (a.t[j].v == a.t[i].v) return false;
+    }
+    return true;
+  }
+
   cdl_status eval_rule(const RuleR& rule, bool first_round) {
+    // the planning pass takes two-atom rules over plain atoms: their first
+    // join writes the head, and setting it up launches nothing
+    if (est_plan && (rule.body.size() != 2 || !plain_atom(rule.body[0]) ||
+                     !plain_atom(rule.body[1])))
+      return CDL_OK;
     // a head relation already marked for an exact redo gains nothing more now
     if (!force_exact && rels[rule.head.rel]->fresh_overflow) return CDL_OK;
     const size_t nb = rule.body.size();
@@ -1575,6 +1635,8 @@ struct cdl_engine {
     const uint32_t nr = (uint32_t)rels.size();
     deferred.clear();
     force_exact = false;
+    est_slot.clear();
+    est_nb = 0;
     cudaError_t e = cudaMemsetAsync(dslot(kSlotCursor), 0, 8 * nr, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dslot(kSlotRoundOverflow), 0, 8, st);
     if (e == cudaSuccess && est_ready()) e = cudaMemsetAsync(join_sizes.p, 0, 8 * kMaxDeferred, st);
@@ -1583,6 +1645,27 @@ struct cdl_engine {
       r->fresh_ub = 0;
       r->fresh_overflow = false;
       r->dense_ub = 0;
+    }
+    if (est_ready() && est_bio.p) {  // the round's predictions, with one wait
+      est_plan = true;
+      cdl_status s = CDL_OK;
+      for (const RuleR& rule : rules)
+        if ((s = eval_rule(rule, round == 1)) != CDL_OK) break;
+      est_plan = false;
+      if (s != CDL_OK) return s;
+      if (est_nb) {
+        float* X = static_cast<float*>(est_bio.p);
+        e = mlp_infer_bf16(ctx, est_wb.p, X, est_nb, X + (size_t)kEstBatch * kMlpIn);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(h_batch, X, sizeof(float) * kMlpIn * est_nb, cudaMemcpyDeviceToHost,
+                              st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(h_batch + (size_t)kEstBatch * kMlpIn, X + (size_t)kEstBatch * kMlpIn,
+                              sizeof(float) * est_nb, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "round predictions");
+        s = fetch(0, 0);
+        if (s != CDL_OK) return s;
+      }
     }
     for (const RuleR& rule : rules) {
       cdl_status s = eval_rule(rule, round == 1);
@@ -1980,6 +2063,10 @@ struct cdl_engine {
       join_sizes = alloc(8 * kMaxDeferred);
       heavy_buf = alloc(256 + sizeof(HeavyChunk) * kHeavyCap);
       if (!join_sizes.p || !heavy_buf.p) return fail(CDL_E_NOMEM, "join sizes");
+      est_bio = alloc(sizeof(float) * kEstBatch * (kMlpIn + 1));
+      if (!est_bio.p || (!h_batch && cudaMallocHost(&h_batch, sizeof(float) * kEstBatch *
+                                                                  (kMlpIn + 1)) != cudaSuccess))
+        return fail(CDL_E_NOMEM, "round predictions");
       heavy.n = static_cast<uint64_t*>(heavy_buf.p);
       heavy.e = reinterpret_cast<HeavyChunk*>(static_cast<char*>(heavy_buf.p) + 256);
       heavy.cap = kHeavyCap;
