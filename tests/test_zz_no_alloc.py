@@ -1,12 +1,15 @@
-"""The allocation-free scan (cdl_exclusive_scan_noalloc) against the
-workspace scan (cdl_exclusive_scan), through the C ABI.
+"""The allocation-free scan (cdl_exclusive_scan_noalloc) through the C ABI,
+against the oracle's exclusive scan and the workspace scan
+(cdl_exclusive_scan).
 
 cdl_exclusive_scan_noalloc serves callers that cannot allocate device
 memory and so cannot hand the library a workspace; it keeps its scratch in a
-fixed array inside the library.  Both calls must give the same offsets and
-total, bit for bit (integer results), on two calls in a row: the second call
-reuses the array the first one left filled.  This file is collected last so
-that a run stopping at the first failure has run every other test."""
+fixed array inside the library.  Its offsets and total must equal the
+oracle's, bit for bit (integer results), on calls in a row: the second call
+scans fewer tiles than the first through the multi-tile passes, so the
+array still holds the first call's tile sums past the second call's last
+tile; the third is a single-tile scan.  This file is collected last so that
+a run stopping at the first failure has run every other test."""
 import ctypes
 
 import numpy as np
@@ -38,19 +41,25 @@ def noalloc_scan(torch, cdl, counts):
     return out[:n], int(total.value)
 
 
-def test_noalloc_scan_matches_workspace_scan_twice(env):
+def test_noalloc_scan_matches_oracle_in_a_row(env):
     torch, cdl = env
+    from oracle import primitives as P
     rng = np.random.default_rng(7)
-    # first call: many tiles with a ragged tail and sums past 2^32;
-    # second call: fewer tiles, so stale tile sums from the first call remain
-    for n in (2048 * 300 + 77, 2048 * 3 + 5):
+    # 1st call: 301 tiles with a ragged tail and sums past 2^32;
+    # 2nd call: 41 tiles (above the single-block cutoff of 65,536 counts), run
+    #           while the array still holds the 1st call's 301 tile sums;
+    # 3rd call: one block, which reads no tile sums at all.
+    for n in (2048 * 300 + 77, 2048 * 40 + 5, 2048 * 3 + 5):
         c = rng.integers(0, 1 << 20, size=n).astype(np.uint32)
         c[n // 3] = 0xFFFFFFFF
         counts = torch.from_numpy(c.view(np.int32)).cuda()
-        want_off, want_total = cdl.exclusive_scan(counts)
+        want_off, want_total = P.exclusive_scan(c)
         got_off, got_total = noalloc_scan(torch, cdl, counts)
         assert got_total == want_total
-        assert torch.equal(got_off, want_off)
+        assert np.array_equal(got_off.cpu().numpy().view(np.uint64), want_off)
+        # and the workspace scan gives the same offsets
+        ws_off, ws_total = cdl.exclusive_scan(counts)
+        assert ws_total == want_total and torch.equal(got_off, ws_off)
 
 
 def test_noalloc_scan_edges(env):
