@@ -243,3 +243,35 @@ def test_invariants_small_programs(oracle_lib):
 def test_max_iters_reports_error(oracle_lib):
     with pytest.raises(RuntimeError):
         oracle_lib.run_program(W.tc_program(W.er_graph(100, 200, 1)), max_iters=2)
+
+
+@pytest.mark.parametrize("n,seed", [(1, 1), (2, 3), (300, 7), (2000, 8), (5000, 2)])
+def test_sg_closed_form_module_matches_oracle(oracle_lib, n, seed):
+    """oracle.closed_forms.sg_forest (vectorised; the form the full-size GPU
+    test uses) against the std::set evaluator and against the pairs it
+    describes: every pair within a (tree, depth) group, x != y."""
+    from oracle import closed_forms as C
+    f = W.random_forest(n, seed, cross_frac=0.0)
+    cf = C.sg_forest(n, f)
+    res = oracle_lib.run_program(W.sg_program(f))
+    got = res.relations["sg"]
+    assert cf["size"] == len(got)
+    assert cf["deltas"] == res.deltas["sg"][:-1] and res.deltas["sg"][-1] == 0
+    assert cf["iterations"] == res.iterations
+    g = cf["group"]
+    want = {(x, y) for x in range(n) for y in range(n) if x != y and g[x] == g[y]} \
+        if n <= 300 else None
+    if want is not None:
+        assert as_set(got) == want
+    # the per-row properties the full-size GPU test checks prove the same set
+    assert np.all(g[got[:, 0]] == g[got[:, 1]]) and np.all(got[:, 0] != got[:, 1])
+    deg = np.bincount(got[:, 0], minlength=n) if len(got) else np.zeros(n, np.int64)
+    assert np.array_equal(deg, cf["group_size"][g] - 1)
+
+
+def test_sg_closed_form_rejects_non_forests():
+    from oracle import closed_forms as C
+    with pytest.raises(ValueError):
+        C.sg_forest(3, np.array([[0, 2], [1, 2]]))
+    with pytest.raises(ValueError):
+        C.sg_forest(3, np.array([[2, 1]]))
