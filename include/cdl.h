@@ -299,6 +299,35 @@ cdl_status cdl_mlp_gradient(const float* params, const float* X, const float* y,
  * accumulation (the engine's prediction path). */
 cdl_status cdl_mlp_infer_bf16(const float* params, const float* X, uint64_t n, float* out,
                               void* workspace, size_t* ws_bytes, void* stream);
+/* One Adam step (Kingma & Ba, 2015: b1 = 0.9, b2 = 0.999, eps = 1e-8, bias
+ * correction with step counted from 1) of the network's training, on
+ * caller-owned device arrays of CDL_MLP_PARAMS floats: params is updated in
+ * place from grad; m and v are the first and second moment estimates (zero
+ * before step 1), updated in place.  CDL_E_INVALID on a NULL array or
+ * step 0.  Asynchronous on stream. */
+cdl_status cdl_mlp_adam(float* params, const float* grad, float* m, float* v, uint64_t step,
+                        float lr, void* stream);
+
+/* The 16 input features of one join, written as floats to the device array
+ * features (the learned estimator is not in the paper; the features read
+ * "delta/full sizes, sampled distinct counts and 32-bucket key histograms"):
+ * a deterministic stride sample of at most 2048 join keys per side (sample
+ * s of n keys is key s * n / min(n, 2048)); each key hashed with the
+ * MurmurHash3 finaliser, h = fmix32(k0 ^ fmix32(k1 + 0x9e3779b9)), k1 = 0
+ * for one-column keys, bucketed by the hash's top 5 bits; distinct counts
+ * of sampled hashes.  probe_k0 / build_k0: device key columns of n_probe /
+ * n_build rows; probe_k1 / build_k1: second key columns or NULL.  host: 6
+ * host floats {|full| of the probe relation, distinct build keys, round,
+ * previous exact output of the step, previous delta of the head relation,
+ * 1 if the step filters else 0}.  Features, in order: log2(1 + x) of probe
+ * rows, build rows, host[0], distinct sampled probe / build hashes, build
+ * rows / max(1, host[1]); log2(1 + histogram join estimate); largest
+ * bucket share (probe, build); bucket entropy in bits (probe, build);
+ * cosine of the two histograms; host[2]; log2(1 + host[3]);
+ * log2(1 + host[4]); host[5].  Asynchronous on stream. */
+cdl_status cdl_join_features(const uint32_t* probe_k0, const uint32_t* probe_k1, uint64_t n_probe,
+                             const uint32_t* build_k0, const uint32_t* build_k1, uint64_t n_build,
+                             const float* host, float* features, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Steps of one round on caller-owned device buffers                          */

@@ -138,6 +138,9 @@ def lib():
         "cdl_mlp_gradient": (ctypes.c_int, [VP, VP, VP, U64, ctypes.c_float, VP, VP, VP,
                                             P(ctypes.c_size_t), VP]),
         "cdl_mlp_infer_bf16": (ctypes.c_int, [VP, VP, U64, VP, VP, P(ctypes.c_size_t), VP]),
+        "cdl_mlp_adam": (ctypes.c_int, [VP, VP, VP, VP, U64, ctypes.c_float, VP]),
+        "cdl_join_features": (ctypes.c_int, [VP, VP, U64, VP, VP, U64, P(ctypes.c_float), VP,
+                                             VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -701,3 +704,31 @@ def mlp_infer_bf16(params, X, stream=None):
     if st != 0:
         raise CdlError(st)
     return out[:n]
+
+
+def mlp_adam(params, grad, m, v, step, lr, stream=None):
+    """One Adam step in place on CUDA float32 tensors of CDL_MLP_PARAMS values."""
+    for t in (params, grad, m, v):
+        _f32(t)
+    st = lib().cdl_mlp_adam(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), step,
+                            lr, _stream_handle(stream))
+    if st != 0:
+        raise CdlError(st)
+
+
+def join_features(probe, build, host, stream=None):
+    """The estimator's 16 features of a join: probe / build are lists of one
+    or two CUDA key columns (int32 tensors, uint32 bit patterns); host the 6
+    host values.  Returns a CUDA float32 tensor of 16."""
+    torch = _torch()
+    for t in list(probe) + list(build):
+        _u32(t)
+    out = torch.empty(MLP_IN, dtype=torch.float32, device=probe[0].device)
+    h = (ctypes.c_float * 6)(*[float(x) for x in host])
+    p1 = probe[1].data_ptr() if len(probe) > 1 else None
+    b1 = build[1].data_ptr() if len(build) > 1 else None
+    st = lib().cdl_join_features(probe[0].data_ptr(), p1, probe[0].numel(), build[0].data_ptr(),
+                                 b1, build[0].numel(), h, out.data_ptr(), _stream_handle(stream))
+    if st != 0:
+        raise CdlError(st)
+    return out

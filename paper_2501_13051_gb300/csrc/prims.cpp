@@ -288,6 +288,25 @@ cdl_status cdl_mlp_infer_bf16(const float* params, const float* X, uint64_t n, f
   return cuda_status(e);
 }
 
+cdl_status cdl_mlp_adam(float* params, const float* grad, float* m, float* v, uint64_t step,
+                        float lr, void* stream) {
+  if (!params || !grad || !m || !v || step == 0) return CDL_E_INVALID;
+  Ctx c;
+  c.st = static_cast<cudaStream_t>(stream);
+  return cuda_status(mlp_adam(c, params, grad, m, v, step, lr));
+}
+
+cdl_status cdl_join_features(const uint32_t* probe_k0, const uint32_t* probe_k1, uint64_t n_probe,
+                             const uint32_t* build_k0, const uint32_t* build_k1, uint64_t n_build,
+                             const float* host, float* features, void* stream) {
+  if (!host || !features || (n_probe && !probe_k0) || (n_build && !build_k0)) return CDL_E_INVALID;
+  JoinFeatureHost hf{host[0], host[1], host[2], host[3], host[4], host[5]};
+  Ctx c;
+  c.st = static_cast<cudaStream_t>(stream);
+  return cuda_status(join_features(c, probe_k0, probe_k1, n_probe, build_k0, build_k1, n_build,
+                                   hf, features));
+}
+
 cdl_status cdl_diff_merge(const uint32_t* const* full, uint64_t n_full,
                           const uint32_t* const* fresh, uint64_t n_fresh, uint32_t arity,
                           uint32_t* const* delta, uint64_t* n_delta, uint32_t* const* merged,

@@ -62,6 +62,67 @@ def test_bf16_inference(cdl):
     assert np.median(np.abs(got - fp) / (1 + np.abs(fp))) <= 0.01
 
 
+def test_adam_kernel_matches_oracle(cdl):
+    """k_adam over four steps (bias correction at t = 1..4, changing
+    gradients) against oracle.mlp.adam in float64."""
+    rng = np.random.default_rng(11)
+    th = rng.normal(size=M.N_PARAMS).astype(np.float32)
+    m = np.zeros(M.N_PARAMS)
+    v = np.zeros(M.N_PARAMS)
+    d_th, d_m, d_v = dev(th), dev(m), dev(v)
+    ref = th.astype(np.float64)
+    for t in range(1, 5):
+        g = (rng.normal(size=M.N_PARAMS) * 10.0 ** rng.integers(-4, 2, size=M.N_PARAMS)).astype(np.float32)
+        cdl.mlp_adam(d_th, dev(g), d_m, d_v, t, 3e-3)
+        ref, m, v = M.adam(ref, g.astype(np.float64), m, v, t, lr=3e-3)
+    got = d_th.cpu().numpy().astype(np.float64)
+    # FP32 state: each step moves a parameter by at most lr, with relative
+    # error ~1e-6; four steps stay well within 1e-5 of the step size
+    assert np.all(np.abs(got - ref) <= 1e-6 + 1e-6 * np.abs(ref))
+    assert np.allclose(d_m.cpu().numpy(), m, rtol=1e-5, atol=1e-9)
+    assert np.allclose(d_v.cpu().numpy(), v, rtol=1e-5, atol=1e-12)
+
+
+def _feature_case(kind, rng):
+    if kind == "uniform":
+        return [rng.integers(0, 1 << 20, 100_000)], [np.sort(rng.integers(0, 1 << 20, 50_000))]
+    if kind == "zipf":
+        return [np.minimum(rng.zipf(1.3, 300_000), 1 << 30)], [np.sort(np.minimum(rng.zipf(1.1, 4000), 1 << 30))]
+    if kind == "small":
+        return [rng.integers(0, 50, 700)], [np.sort(rng.integers(0, 50, 33))]
+    if kind == "equal":
+        return [np.full(5000, 7)], [np.full(3000, 7)]
+    if kind == "two-column":
+        return ([rng.integers(0, 300, 9000), rng.integers(0, 5, 9000)],
+                [rng.integers(0, 300, 2049), rng.integers(0, 5, 2049)])
+    if kind == "empty-probe":
+        return [np.zeros(0, np.int64)], [np.arange(100)]
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "zipf", "small", "equal", "two-column",
+                                  "empty-probe"])
+def test_join_features_match_oracle(cdl, kind):
+    """k_join_features against the float64 statement of the 16 features
+    (oracle.features): distinct counts exact, the rest to FP32 rounding."""
+    import torch
+    from oracle import features as F
+    rng = np.random.default_rng(len(kind))
+    probe, build = _feature_case(kind, rng)
+    probe = [np.asarray(c, dtype=np.uint32) for c in probe]
+    build = [np.asarray(c, dtype=np.uint32) for c in build]
+    host = (float(3 * len(probe[0]) + 1), float(len(np.unique(build[0]))), 4.0, 1234.0, 567.0,
+            1.0 if kind == "small" else 0.0)
+    to = lambda a: torch.from_numpy(a.view(np.int32)).cuda()
+    got = cdl.join_features([to(c) for c in probe], [to(c) for c in build], host).cpu().numpy()
+    want = F.join_features(probe[0], build[0], host,
+                           probe_k1=probe[1] if len(probe) > 1 else None,
+                           build_k1=build[1] if len(build) > 1 else None)
+    assert np.all(np.abs(got - want) <= 1e-5 + 1e-5 * np.abs(want)), (got, want)
+    # the distinct counts are integers on both sides
+    assert np.array_equal(np.round(2.0 ** got[3:5] - 1), np.round(2.0 ** want[3:5] - 1))
+
+
 def log_joins(cdl, programs):
     X, y = [], []
     for prog in programs:

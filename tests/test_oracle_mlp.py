@@ -67,3 +67,38 @@ def test_bf16_rounding():
     assert r[4] == 65536.0
     # 8 significant bits survive: relative error <= 2^-9
     assert np.all(np.abs(r - vals) <= np.abs(vals) * 2.0 ** -8)
+
+
+def test_adam_constant_gradient_closed_form():
+    # with a constant gradient g, m_t = g (1 - b1^t) and v_t = g^2 (1 - b2^t),
+    # so the bias-corrected step is lr g / (|g| + eps) at every t
+    g = np.array([0.3, -2.0, 1e-3, -5e-4, 7.0])
+    th, m, v = np.ones(5), np.zeros(5), np.zeros(5)
+    lr, eps, T = 0.01, 1e-8, 50
+    for t in range(1, T + 1):
+        th, m, v = M.adam(th, g, m, v, t, lr=lr, eps=eps)
+    assert np.allclose(th, 1.0 - T * lr * g / (np.abs(g) + eps), rtol=0, atol=1e-12)
+    assert np.allclose(m, g * (1 - 0.9 ** T)) and np.allclose(v, g * g * (1 - 0.999 ** T))
+
+
+def test_forward_bf16_hand_computed():
+    # unit 0: x0 -> 3 x0 -> h1 -> h2 -> out; unit 1 is cut by the ReLU.
+    # x0 = 1.005859375 rounds to 1.0078125 (bf16 spacing 2^-7 in [1, 2));
+    # 3 * 1.0078125 = 3.0234375 lies halfway between 3.015625 and 3.03125
+    # (spacing 2^-6 in [2, 4)) and rounds to the even 3.03125;
+    # b3 = 0.1f rounds to 0.10009765625.
+    p = {k: np.zeros(s) for k, s in M.SIZES}
+    p["W1"][0, 0], p["W1"][1, 0] = 3.0, -1.0
+    p["W2"][0, 0], p["W2"][1, 1] = 1.0, 1.0
+    p["w3"][0], p["w3"][1] = 1.0, 5.0
+    p["b3"][0] = np.float32(0.1)
+    x = np.zeros((1, M.D_IN), dtype=np.float32)
+    x[0, 0] = 1.005859375
+    got = M.forward_bf16(M.pack(p), x)[0]
+    assert got == 3.03125 + 0.10009765625
+    # neither rounding skipped: without the input's, 3 * 1.005859375 rounds
+    # to 3.015625; without h1's the value would be 3.0234375
+    assert abs(got - (3.015625 + 0.10009765625)) > 1e-3
+    assert abs(got - (3.0234375 + 0.10009765625)) > 1e-3
+    # the float64 forward keeps every digit
+    assert M.forward(M.pack(p), x)[0][0] == pytest.approx(3 * 1.005859375 + float(np.float32(0.1)))
