@@ -90,7 +90,8 @@ typedef struct {
   int32_t estimator;   /* join-size estimator: 0 off; 1 predict (once trained or set);
                           2 predict and log every join's features and exact size */
   double hash_load;    /* hash table load factor in (0, 0.9]; 0 = default 0.5 */
-  uint32_t radix_bits; /* radix digit width 8 or 10; 0 = default 8 */
+  uint32_t radix_bits; /* radix digit width 8, 9 or 10; 0 = default: 8, or 9 where 9-bit
+                         digits take one pass fewer (36-bit keys: 4 passes, not 5) */
   const char* log_path; /* reserved, must be NULL */
   double est_margin;   /* predicted buffers hold 2^(prediction + est_margin) tuples;
                           0 = default 1.0 (negative values force fallbacks in tests); every
@@ -122,7 +123,8 @@ typedef struct {
                            bits in all keeps its new tuples of a round as a bitmap of 2^T
                            bits: join outputs set bits instead of being written, and the
                            bits read back in order are the sorted unique tuples (no radix
-                           sort).  0 = default 28; -1 = never.  Results never depend on it */
+                           sort).  0 = default 28; -1 = never; values above 34 act as 34
+                           (a 2 GB bitmap).  Results never depend on it */
 } cdl_options;
 
 /* Fills *opts with the defaults (everything zero / NULL except the

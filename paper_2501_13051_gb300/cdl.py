@@ -234,7 +234,7 @@ class Engine:
     from KERNEL_CLASSES (events wrap only those launches)."""
 
     def __init__(self, *, device=None, stream=None, mem_limit=0, max_iters=0, spin_limit=0,
-                 timing=False, hash_load=0.5, radix_bits=8, torch_alloc=True, estimator=0,
+                 timing=False, hash_load=0.5, radix_bits=0, torch_alloc=True, estimator=0,
                  est_margin=1.0, est_params=None, n_instances=0, retire=True, autotune=0,
                  tune_cache=None, graph=False, est_min_rows=0, dense_bits=0):
         torch = _torch()

@@ -342,7 +342,10 @@ struct cdl_engine {
   DBuf ctl;
   uint64_t* h_ctl = nullptr;
   std::vector<std::unique_ptr<Index>> cache;
-  uint32_t radix_bits = 8;
+  uint32_t radix_bits = 0;  // digit width 8, 9 or 10; 0: 8, or 9 where that saves a pass
+  uint32_t digits_for(uint32_t total_bits) const {
+    return radix_bits ? radix_bits : fit_digit_bits(total_bits, 8);
+  }
   double hash_load = 0.5;
   Tuner tuner;
   uint64_t joins = 0;
@@ -372,6 +375,7 @@ struct cdl_engine {
   static constexpr double kDirectMaxTuples = double(1 << 24);
   static constexpr uint64_t kPredictMinRows = 1 << 15;  // smaller probes keep the count pass
   static constexpr int kDenseBits = 28;  // default bound of a dense relation's tuple space (32 MB)
+  static constexpr int kDenseBitsMax = 34;  // largest bitmap form accepted (2 GB per relation)
   static constexpr uint64_t kGroupRows = 1 << 21;  // larger new-tuple sets sort on their own
   static constexpr size_t kGroupMin = 4;           // fewer relations sort one by one
   struct Deferred {
@@ -576,14 +580,15 @@ struct cdl_engine {
     int cand = 0;
     bool measure = false;
     std::string key;
+    uint32_t total = 0;
+    for (uint32_t k = 0; k < d.k; ++k) total += bits[k];
     if (tuner.mode && d.n >= (1u << 14)) {
-      uint32_t total = 0;
-      for (uint32_t k = 0; k < d.k; ++k) total += bits[k];
       key = "sort.k" + std::to_string(d.k) + ".b" + std::to_string(total) + ".n" +
             std::to_string(bits_of(d.n));
       cand = tuner.choose(key, 4, &measure);
     }
-    const uint32_t digit = (cand & 1) ? (radix_bits == 8 ? 10 : 8) : radix_bits;
+    const uint32_t base = digits_for(total);
+    const uint32_t digit = (cand & 1) ? (base == 10 ? 8 : 10) : base;
     RadixPlan plan = make_radix_plan(d.k, bits, digit, (cand & 2) ? 256 : 512);
     if (plan.npass == 0) return CDL_OK;
     DCols alt;
@@ -1301,7 +1306,7 @@ struct cdl_engine {
       if (!R.idb || opt.n_instances || dmax <= 0 || R.arity == 0) continue;
       uint32_t bits[kMaxK], T = 0;
       for (uint32_t k = 0; k < R.arity; ++k) T += bits[k] = bits_of(R.bound[k]);
-      if (T > (uint32_t)std::min(dmax, 30)) continue;
+      if (T > (uint32_t)std::min(dmax, kDenseBitsMax)) continue;
       const uint64_t nw = T >= 5 ? (1ull << (T - 5)) : 1;
       R.dset_buf = alloc(4 * nw);
       if (!R.dset_buf.p) return fail(CDL_E_NOMEM, "dense set");
@@ -1803,7 +1808,7 @@ struct cdl_engine {
       uint32_t total_bits = 0;
       for (uint32_t k = 0; k < R.arity; ++k) total_bits += bits[k];
       const bool wide = G.Ucap <= (1u << 18) && (total_bits + 9) / 10 < (total_bits + 7) / 8;
-      G.plan = make_radix_plan(R.arity, bits, wide ? 10 : radix_bits, 512);
+      G.plan = make_radix_plan(R.arity, bits, wide ? 10 : digits_for(total_bits), 512);
       G.sorted_in_alt = G.plan.npass % 2 == 1;
       bool ok = true;
       for (int side = 0; side < 2; ++side) {
@@ -2556,7 +2561,7 @@ void cdl_options_default(cdl_options* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
   o->hash_load = 0.5;
-  o->radix_bits = 8;
+  o->radix_bits = 0;
 }
 
 cdl_status cdl_create(const cdl_options* opts, cdl_engine** out) {
@@ -2571,7 +2576,7 @@ cdl_status cdl_create(const cdl_options* opts, cdl_engine** out) {
   e->pool.ctx = e->opt.alloc_ctx;
   e->pool.limit = e->opt.mem_limit;
   e->hash_load = (e->opt.hash_load > 0 && e->opt.hash_load <= 0.9) ? e->opt.hash_load : 0.5;
-  e->radix_bits = e->opt.radix_bits == 10 ? 10 : 8;
+  e->radix_bits = (e->opt.radix_bits >= 8 && e->opt.radix_bits <= 10) ? e->opt.radix_bits : 0;
   e->tuner.mode = e->opt.autotune < 0 ? 0 : (e->opt.autotune > 2 ? 2 : e->opt.autotune);
   e->tuner.path = e->opt.tune_cache ? e->opt.tune_cache : "";
   e->opt.tune_cache = nullptr;  // the engine keeps its own copy of the path

@@ -171,6 +171,9 @@ struct RadixPlan {
   };
   std::vector<Pass> pass;
 };
+// Digit width for a key of total_bits: 9 where 9-bit digits take one pass
+// fewer than 8-bit ones (36-bit keys: 4 passes instead of 5), else base.
+uint32_t fit_digit_bits(uint32_t total_bits, uint32_t base);
 // col_bits[k]: significant bits of column k (all values < 2^col_bits[k]).
 RadixPlan make_radix_plan(uint32_t k, const uint32_t* col_bits, uint32_t digit_bits,
                           uint32_t threads = 512);

@@ -16,6 +16,8 @@
 // row-major), b2, w3 (64), b3: 5313 values.
 #include <cuda_bf16.h>
 
+#include <cmath>
+
 #include "kernels.h"
 
 namespace cdl {
@@ -113,14 +115,16 @@ __global__ void k_mlp_param_grads(const float* __restrict__ X, uint64_t n,
   grad[p] = acc;
 }
 
+// b1, b2 and their complements ob1 = 1 - b1, ob2 = 1 - b2 come rounded
+// from double (1 - 0.999f in float would be 1.3e-5 off 0.001).
 __global__ void k_adam(float* __restrict__ th, const float* __restrict__ grad,
                        float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
-                       float eps, float c1, float c2) {
+                       float ob1, float ob2, float eps, float c1, float c2) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= kMlpParams) return;
   const float g = grad[p];
-  const float mm = b1 * m[p] + (1.f - b1) * g;
-  const float vv = b2 * v[p] + (1.f - b2) * g * g;
+  const float mm = b1 * m[p] + ob1 * g;
+  const float vv = b2 * v[p] + ob2 * g * g;
   m[p] = mm;
   v[p] = vv;
   th[p] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
@@ -265,10 +269,13 @@ cudaError_t mlp_gradient(Ctx& c, const float* th, const float* X, const float* y
 
 cudaError_t mlp_adam(Ctx& c, float* th, const float* grad, float* m, float* v, uint64_t step,
                      float lr) {
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  const double b1 = 0.9, b2 = 0.999;
+  const float c1 = (float)(1.0 - std::pow(b1, (double)step));
+  const float c2 = (float)(1.0 - std::pow(b2, (double)step));
   ProfScope p(c, kMlp, 0.0);
-  k_adam<<<(kMlpParams + 255) / 256, 256, 0, c.st>>>(th, grad, m, v, lr, b1, b2, 1e-8f, c1, c2);
+  k_adam<<<(kMlpParams + 255) / 256, 256, 0, c.st>>>(th, grad, m, v, lr, (float)b1, (float)b2,
+                                                      (float)(1.0 - b1), (float)(1.0 - b2), 1e-8f,
+                                                      c1, c2);
   return cudaGetLastError();
 }
 

@@ -193,7 +193,7 @@ cdl_status cdl_sort_unique(const uint32_t* const* cols, uint32_t arity, uint64_t
   if (!ws_bytes || arity < 1 || arity > CDL_MAX_ARITY) return CDL_E_INVALID;
   const uint64_t rows = n ? n : 1;
   const size_t col = up(rows * 4);
-  const size_t need = kHead + 2 * arity * col + up(radix_workspace(n, 8)) +
+  const size_t need = kHead + 2 * arity * col + up(radix_workspace(n, 9)) +
                       up(diff_merge_workspace(0, n));
   if (!workspace) {
     *ws_bytes = need;
@@ -206,7 +206,7 @@ cdl_status cdl_sort_unique(const uint32_t* const* cols, uint32_t arity, uint64_t
   ColsOut a{}, b{};
   for (uint32_t k = 0; k < arity; ++k) a.c[k] = static_cast<uint32_t*>(cv.take(rows * 4));
   for (uint32_t k = 0; k < arity; ++k) b.c[k] = static_cast<uint32_t*>(cv.take(rows * 4));
-  void* rws = cv.take(radix_workspace(n, 8));
+  void* rws = cv.take(radix_workspace(n, 9));  // room for 9-bit digits
   void* dws = cv.take(diff_merge_workspace(0, n));
   Ctx c;
   c.st = static_cast<cudaStream_t>(stream);
@@ -225,7 +225,9 @@ cdl_status cdl_sort_unique(const uint32_t* const* cols, uint32_t arity, uint64_t
   uint32_t bits[kMaxK] = {0, 0, 0, 0};
   const uint32_t* hm = reinterpret_cast<const uint32_t*>(h + 4);
   for (uint32_t k = 0; k < arity; ++k) bits[k] = bits_of(hm[k]);
-  RadixPlan plan = make_radix_plan(arity, bits, 8);
+  uint32_t total = 0;
+  for (uint32_t k = 0; k < arity; ++k) total += bits[k];
+  RadixPlan plan = make_radix_plan(arity, bits, fit_digit_bits(total, 8));
   bool in_b = false;
   e = radix_sort(c, plan, a, b, n, rws, &in_b);
   if (e != cudaSuccess) return CDL_E_CUDA;

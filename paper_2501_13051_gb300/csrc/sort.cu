@@ -109,14 +109,14 @@ __global__ void __launch_bounds__(T, 1536 / T) k_radix_scatter(ColsIn in, ColsOu
     const uint64_t idx = wbase + (uint64_t)it * 32 + lane;
     const bool valid = idx < n;
     const uint32_t d = valid ? digit_of<K>(v[it], p) : (uint32_t)R;
+    // lanes holding the same digit: the lowest one advances the warp's
+    // count of that digit for all of them and hands out the old count
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t before = __popc(peers & lt);
+    const uint32_t leader = (uint32_t)__ffs(peers) - 1u;
     uint32_t b = 0;
-    if (valid) b = wh[warp][d];
-    __syncwarp();
-    if (valid && before == 0) wh[warp][d] = b + __popc(peers);
-    __syncwarp();
-    rk[it] = b + before;
+    if (valid && lane == leader) b = atomicAdd(&wh[warp][d], (uint32_t)__popc(peers));
+    b = __shfl_sync(0xffffffffu, b, leader);
+    rk[it] = b + __popc(peers & lt);
   }
   __syncthreads();
   // per digit: exclusive offsets across warps (warp order = input order)
@@ -254,6 +254,9 @@ cudaError_t sort_k(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t
     case 8:
       return wide ? sort_passes<K, 8, 512>(c, plan, a, b, n, ws, in_b, dn)
                   : sort_passes<K, 8, 256>(c, plan, a, b, n, ws, in_b, dn);
+    case 9:
+      return wide ? sort_passes<K, 9, 512>(c, plan, a, b, n, ws, in_b, dn)
+                  : sort_passes<K, 9, 256>(c, plan, a, b, n, ws, in_b, dn);
     case 10:
       return wide ? sort_passes<K, 10, 512>(c, plan, a, b, n, ws, in_b, dn)
                   : sort_passes<K, 10, 256>(c, plan, a, b, n, ws, in_b, dn);
@@ -263,11 +266,17 @@ cudaError_t sort_k(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint64_t
 
 }  // namespace
 
+uint32_t fit_digit_bits(uint32_t total_bits, uint32_t base) {
+  if (base != 8) return base;
+  const uint32_t p8 = (total_bits + 7) / 8;
+  return (p8 > 1 && total_bits <= 9 * (p8 - 1)) ? 9u : 8u;
+}
+
 RadixPlan make_radix_plan(uint32_t k, const uint32_t* col_bits, uint32_t digit_bits,
                           uint32_t threads) {
   RadixPlan pl;
   pl.k = k;
-  pl.bits = (digit_bits == 10) ? 10 : 8;
+  pl.bits = (digit_bits == 10 || digit_bits == 9) ? digit_bits : 8;
   pl.threads = threads == 256 ? 256 : 512;
   uint32_t pos[kMaxK] = {0, 0, 0, 0};
   uint32_t total = 0;
@@ -294,7 +303,7 @@ RadixPlan make_radix_plan(uint32_t k, const uint32_t* col_bits, uint32_t digit_b
 }
 
 size_t radix_workspace(uint64_t n, uint32_t digit_bits, uint32_t threads) {
-  const uint64_t R = 1ull << (digit_bits == 10 ? 10 : 8);
+  const uint64_t R = 1ull << ((digit_bits == 10 || digit_bits == 9) ? digit_bits : 8);
   const uint64_t tile = (threads == 256 ? 256 : 512) * kRItems;
   const uint64_t ntiles = (n + tile - 1) / tile;
   const uint64_t cells = R * ntiles;

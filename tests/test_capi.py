@@ -31,7 +31,7 @@ def test_every_declared_symbol_is_exported(libcdl):
 def test_host_only_calls(libcdl):
     o = cdl.Options()
     libcdl.cdl_options_default(ctypes.byref(o))
-    assert o.hash_load == 0.5 and o.radix_bits == 8 and o.max_iters == 0
+    assert o.hash_load == 0.5 and o.radix_bits == 0 and o.max_iters == 0
     # 16-byte slots, power-of-two count, load factor respected
     for n, load in ((0, 0.5), (1, 0.5), (1000, 0.5), (1000, 0.8), (1 << 20, 0.5)):
         b = libcdl.cdl_hash_table_bytes(n, load)

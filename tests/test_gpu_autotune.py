@@ -49,7 +49,7 @@ def test_tuning_runs_cover_every_candidate(cdl, oracle_lib, tmp_path):
     assert np.array_equal(got["sg"], want.relations["sg"])
 
 
-@pytest.mark.parametrize("radix_bits", [8, 10])
+@pytest.mark.parametrize("radix_bits", [0, 8, 9, 10])
 def test_every_sort_candidate_is_exact(cdl, tmp_path, radix_bits):
     # a larger forest: sorts and indexes past the tuner's size thresholds
     prog = W.sg_program(W.random_forest(40000, 22))

@@ -71,15 +71,18 @@ def test_adam_kernel_matches_oracle(cdl):
     v = np.zeros(M.N_PARAMS)
     d_th, d_m, d_v = dev(th), dev(m), dev(v)
     ref = th.astype(np.float64)
+    m_abs = np.zeros(M.N_PARAMS)  # the first moment's terms in magnitude
     for t in range(1, 5):
         g = (rng.normal(size=M.N_PARAMS) * 10.0 ** rng.integers(-4, 2, size=M.N_PARAMS)).astype(np.float32)
         cdl.mlp_adam(d_th, dev(g), d_m, d_v, t, 3e-3)
         ref, m, v = M.adam(ref, g.astype(np.float64), m, v, t, lr=3e-3)
+        m_abs = 0.9 * m_abs + 0.1 * np.abs(g)
     got = d_th.cpu().numpy().astype(np.float64)
     # FP32 state: each step moves a parameter by at most lr, with relative
     # error ~1e-6; four steps stay well within 1e-5 of the step size
     assert np.all(np.abs(got - ref) <= 1e-6 + 1e-6 * np.abs(ref))
-    assert np.allclose(d_m.cpu().numpy(), m, rtol=1e-5, atol=1e-9)
+    # FP32 rounding relative to the terms summed (m may cancel to near 0)
+    assert np.all(np.abs(d_m.cpu().numpy() - m) <= 1e-6 * m_abs + 1e-12)
     assert np.allclose(d_v.cpu().numpy(), v, rtol=1e-5, atol=1e-12)
 
 

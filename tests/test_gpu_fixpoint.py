@@ -104,7 +104,7 @@ def test_random_programs(cdl, oracle_lib, seed, dense):
     check(cdl, oracle_lib, W.random_program(seed), dense_bits=dense)
 
 
-@pytest.mark.parametrize("opts", [dict(radix_bits=10), dict(hash_load=0.8), dict(timing=True)])
+@pytest.mark.parametrize("opts", [dict(radix_bits=8), dict(radix_bits=9), dict(radix_bits=10), dict(hash_load=0.8), dict(timing=True)])
 def test_engine_options_do_not_change_results(cdl, oracle_lib, opts):
     check(cdl, oracle_lib, W.sg_program(W.random_forest(1500, 5)), **opts)
 
