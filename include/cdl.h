@@ -125,6 +125,19 @@ typedef struct {
                            bits read back in order are the sorted unique tuples (no radix
                            sort).  0 = default 28; -1 = never; values above 34 act as 34
                            (a 2 GB bitmap).  Results never depend on it */
+  int32_t dedup;        /* step (d) of derived relations whose Full no rule variant reads
+                           after round 1 (every rule naming them has no other derived body
+                           atom; batched runs excluded): 0 = default, the difference and
+                           merge of sorted rows; 1 = Algorithm 2 (Section 4, "Union and
+                           Deduplication"): Full kept in the decomposed storage model of
+                           Section 3 (rows in insertion order, per column a sorted index of
+                           surrogate ids and the unique hashmap over it), a new tuple is in
+                           Full when the id ranges of its values overlap, delta is appended
+                           and merged into each column's sorted index; 2 = the same with a
+                           hash-only index (one multimap of column 0's (value, id) entries),
+                           the alternative Section 3 argues against.  Full is sorted back
+                           into rows when the run ends.  No graph rounds with 1 or 2.
+                           Results never depend on it */
 } cdl_options;
 
 /* Fills *opts with the defaults (everything zero / NULL except the

@@ -45,7 +45,7 @@ class Options(ctypes.Structure):
                 ("n_instances", ctypes.c_uint32), ("retire", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("tune_cache", ctypes.c_char_p),
                 ("est_min_rows", ctypes.c_uint64), ("graph", ctypes.c_int32),
-                ("dense_bits", ctypes.c_int32)]
+                ("dense_bits", ctypes.c_int32), ("dedup", ctypes.c_int32)]
 
 MLP_IN = 16
 MLP_PARAMS = 5313
@@ -212,7 +212,7 @@ class RunStats:
 # kernel classes in cdl_kernel_profile order
 KERNEL_CLASSES = ("hash_build", "count_heads", "join_count", "scan", "join_write",
                   "radix_upsweep", "radix_scatter", "diff_count", "diff_merge", "select",
-                  "misc", "estimator", "join_direct", "retire", "dense")
+                  "misc", "estimator", "join_direct", "retire", "dense", "dedup")
 
 
 def _timing_mask(timing):
@@ -236,7 +236,7 @@ class Engine:
     def __init__(self, *, device=None, stream=None, mem_limit=0, max_iters=0, spin_limit=0,
                  timing=False, hash_load=0.5, radix_bits=0, torch_alloc=True, estimator=0,
                  est_margin=1.0, est_params=None, n_instances=0, retire=True, autotune=0,
-                 tune_cache=None, graph=False, est_min_rows=0, dense_bits=0):
+                 tune_cache=None, graph=False, est_min_rows=0, dense_bits=0, dedup=0):
         torch = _torch()
         L = lib()
         self._L = L
@@ -263,6 +263,7 @@ class Engine:
         opts.graph = int(graph)  # True / False, or a starting capacity in rows
         opts.est_min_rows = est_min_rows
         opts.dense_bits = dense_bits  # 0 default (28), -1 never
+        opts.dedup = dedup  # 0 merge of sorted rows, 1 Algorithm 2 (hybrid index), 2 hash-only
         opts.tune_cache = os.fsencode(tune_cache) if tune_cache else None
         self.n_instances = n_instances
         self._opts = opts

@@ -245,6 +245,35 @@ uint32_t bits_of(uint64_t v) {
 
 enum Ver { kFull = 0, kDelta = 1 };
 
+// Full of a derived relation in the decomposed storage model, for the
+// Algorithm 2 form of step (d) (option dedup; kernels in dsm.cu): rows in
+// insertion order (row = surrogate id), and per column k its sorted index,
+// kept as (value, id) pairs in (value, id) order, with the unique hashmap
+// over the values (dedup 1), or one multimap of column 0's (value, id)
+// entries (dedup 2).  Each round appends delta to the rows, merges delta's
+// entries into each column's sorted index and rebuilds the hashmaps.
+struct Dsm {
+  bool on = false;    // the relation's step (d) is Algorithm 2
+  bool init = false;  // built from the relation's rows at its first merge
+  DCols raw;          // rows in insertion order; raw.n rows
+  DCols idx[kMaxK];   // column k: c[0] values ascending, c[1] ids (ascending per value)
+  DBuf table[kMaxK];  // column k's unique hashmap over idx[k].c[0]
+  uint64_t slots[kMaxK] = {0, 0, 0, 0};
+  DBuf mm;            // hash-only: multimap of column 0
+  uint64_t mm_slots = 0;
+  void reset() {
+    on = init = false;
+    raw.clear();
+    for (int k = 0; k < kMaxK; ++k) {
+      idx[k].clear();
+      table[k].reset();
+      slots[k] = 0;
+    }
+    mm.reset();
+    mm_slots = 0;
+  }
+};
+
 struct Relation {
   std::string name;
   uint32_t arity = 0;
@@ -267,6 +296,7 @@ struct Relation {
   DBuf dset_buf;
   uint64_t dense_ub = 0;  // tuples sent to dset this round: a bound on its bits
   DCols dense_rows;
+  Dsm dsm;
 };
 
 struct Term {
@@ -610,6 +640,7 @@ struct cdl_engine {
 
   // merged = full U fresh (fresh sorted, repeats allowed); delta = fresh - full.
   cdl_status merge_into(Relation& r, DCols& fresh, DCols* delta_out, uint32_t delta_slot) {
+    if (r.dsm.on) return dsm_diff(r, fresh, delta_out, delta_slot);
     DCols merged, delta;
     if (!alloc_cols(merged, r.arity, r.full.n + fresh.n) || !alloc_cols(delta, r.arity, fresh.n))
       return fail(CDL_E_NOMEM, "merge buffers");
@@ -622,6 +653,217 @@ struct cdl_engine {
     r.full = std::move(merged);
     r.version[kFull]++;
     if (delta_out) *delta_out = std::move(delta);
+    return CDL_OK;
+  }
+
+  // ------------------------------------------- Algorithm 2 (option dedup)
+  // Derived relations whose Full no rule variant reads after round 1 (every
+  // rule that names them has no other derived body atom, so its semi-naive
+  // variant reads their delta only) keep Full in the decomposed form.
+  void dsm_select() {
+    std::vector<uint8_t> full_read(rels.size(), 0);
+    for (const RuleR& r : rules) {
+      uint32_t nidb = 0;
+      for (const AtomR& a : r.body) nidb += rels[a.rel]->idb ? 1u : 0u;
+      if (nidb >= 2)
+        for (const AtomR& a : r.body)
+          if (rels[a.rel]->idb) full_read[a.rel] = 1;
+    }
+    for (size_t i = 0; i < rels.size(); ++i) {
+      Relation& R = *rels[i];
+      R.dsm.reset();
+      R.dsm.on = opt.dedup > 0 && R.idb && !full_read[i] && !opt.n_instances;
+    }
+  }
+
+  DsmView dsm_view(const Relation& R) const {
+    DsmView v;
+    v.raw = R.dsm.raw.in();
+    v.n = R.dsm.raw.n;
+    for (uint32_t k = 0; k < R.arity; ++k) {
+      v.ids[k] = R.dsm.idx[k].c[1];
+      v.table[k] = static_cast<const Slot*>(R.dsm.table[k].p);
+      v.mask[k] = R.dsm.slots[k] ? R.dsm.slots[k] - 1 : 0;
+    }
+    v.mm = static_cast<const uint2*>(R.dsm.mm.p);
+    v.mm_mask = R.dsm.mm_slots ? R.dsm.mm_slots - 1 : 0;
+    return v;
+  }
+
+  // The unique hashmap of every column over its sorted index.
+  cdl_status dsm_tables(Relation& R) {
+    Dsm& D = R.dsm;
+    for (uint32_t k = 0; k < R.arity; ++k) {
+      uint64_t distinct = 0;
+      if (D.raw.n) {
+        cudaError_t e = count_heads(ctx, D.idx[k].c[0], nullptr, D.raw.n, dslot(kSlotScratch));
+        if (e != cudaSuccess) return cuda_fail(e, "count_heads");
+        cdl_status r = fetch(kSlotScratch, 1);
+        if (r != CDL_OK) return r;
+        distinct = h_ctl[kSlotScratch];
+      }
+      const uint64_t slots = table_slots(distinct, hash_load);
+      if (slots != D.slots[k] || !D.table[k].p) {
+        D.table[k] = alloc(slots * sizeof(Slot));
+        if (!D.table[k].p) return fail(CDL_E_NOMEM, "decomposed hashmap");
+        D.slots[k] = slots;
+      }
+      cudaError_t e = hash_build(ctx, D.idx[k].c[0], nullptr, D.raw.n,
+                                 static_cast<Slot*>(D.table[k].p), slots);
+      if (e != cudaSuccess) return cuda_fail(e, "hash_build");
+    }
+    return CDL_OK;
+  }
+
+  // Multimap of column 0 sized for cap rows at load 0.5, holding rows [0, n).
+  cdl_status dsm_multimap(Relation& R, uint64_t cap) {
+    Dsm& D = R.dsm;
+    D.mm_slots = table_slots(cap, 0.5);
+    D.mm = alloc(D.mm_slots * 8);
+    if (!D.mm.p) return fail(CDL_E_NOMEM, "decomposed multimap");
+    cudaError_t e = cudaMemsetAsync(D.mm.p, 0xFF, D.mm_slots * 8, st);
+    if (e == cudaSuccess)
+      e = mm_insert(ctx, D.raw.c[0], D.raw.n, 0, static_cast<uint2*>(D.mm.p), D.mm_slots);
+    return e == cudaSuccess ? CDL_OK : cuda_fail(e, "multimap");
+  }
+
+  // Column k's (value, id) entries of rows [first, first + n) of src, in
+  // (value, id) order: src is sorted with column 0 first, so column 0's
+  // entries already are; the others sort by value, stably (ids ascend).
+  cdl_status dsm_entries(const Relation& R, const DCols& src, uint32_t k, uint64_t first,
+                         DCols& out) {
+    const uint64_t n = src.n;
+    if (!alloc_cols(out, 2, n)) return fail(CDL_E_NOMEM, "index entries");
+    out.n = n;
+    cudaError_t e = n ? cudaMemcpyAsync(out.c[0], src.c[k], n * 4, cudaMemcpyDeviceToDevice, st)
+                      : cudaSuccess;
+    if (e == cudaSuccess) e = iota_u32(ctx, out.c[1], n, (uint32_t)first);
+    if (e != cudaSuccess) return cuda_fail(e, "index entries");
+    if (k == 0 || n <= 1) return CDL_OK;
+    const uint32_t bits[2] = {bits_of(R.bound[k]), 0};  // by value only: a stable pass keeps ids ascending
+    return sort_cols(out, bits);
+  }
+
+  // Full, as loaded or left by round 1, becomes the decomposed form.
+  cdl_status dsm_build(Relation& R) {
+    Dsm& D = R.dsm;
+    const uint64_t n0 = R.full.n;
+    if (!alloc_cols(D.raw, R.arity, std::max<uint64_t>(2 * n0, 1 << 16)))
+      return fail(CDL_E_NOMEM, "decomposed rows");
+    for (uint32_t k = 0; k < R.arity && n0; ++k) {
+      cudaError_t e = cudaMemcpyAsync(D.raw.c[k], R.full.c[k], n0 * 4, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "decomposed rows");
+    }
+    D.raw.n = n0;
+    cdl_status r = CDL_OK;
+    if (opt.dedup == 1) {
+      for (uint32_t k = 0; k < R.arity && r == CDL_OK; ++k) r = dsm_entries(R, R.full, k, 0, D.idx[k]);
+      if (r == CDL_OK) r = dsm_tables(R);
+    } else {
+      r = dsm_multimap(R, D.raw.cap);
+    }
+    if (r != CDL_OK) return r;
+    R.full.clear();  // the rows live in the decomposed form until the run ends
+    R.full.k = R.arity;
+    R.full.n = n0;
+    D.init = true;
+    return CDL_OK;
+  }
+
+  // Step (d) by Algorithm 2: delta = the sorted fresh rows that repeat
+  // neither their predecessor nor a row of Full; |delta| into delta_slot.
+  cdl_status dsm_diff(Relation& R, DCols& fresh, DCols* delta_out, uint32_t delta_slot) {
+    if (!R.dsm.init) {
+      cdl_status r = dsm_build(R);
+      if (r != CDL_OK) return r;
+    }
+    const uint64_t n = fresh.n;
+    DBuf flags = alloc(4 * (n ? n : 1)), off = alloc(8 * (n ? n : 1)), ws = alloc(scan_workspace(n));
+    DCols delta;
+    if (!flags.p || !off.p || !ws.p || !alloc_cols(delta, R.arity, n))
+      return fail(CDL_E_NOMEM, "dedup buffers");
+    const DsmView v = dsm_view(R);
+    uint32_t* f = static_cast<uint32_t*>(flags.p);
+    uint64_t* o = static_cast<uint64_t*>(off.p);
+    cudaError_t e = dsm_probe(ctx, R.arity, fresh.in(), n, v, opt.dedup == 2, f);
+    if (e == cudaSuccess) e = exclusive_scan(ctx, f, n, o, dslot(delta_slot), ws.p);
+    if (e == cudaSuccess) e = compact_rows(ctx, R.arity, fresh.in(), n, f, o, delta.out());
+    if (e != cudaSuccess) return cuda_fail(e, "dedup");
+    R.version[kFull]++;
+    if (delta_out) *delta_out = std::move(delta);
+    return CDL_OK;
+  }
+
+  // The union, once |delta| is known: delta appended to the rows (new ids
+  // n0 ..), its entries merged into every column's sorted index, the
+  // hashmaps rebuilt (or delta's column 0 added to the multimap).
+  cdl_status dsm_append(Relation& R) {
+    Dsm& D = R.dsm;
+    const uint64_t n0 = D.raw.n, nd = R.delta.n, n1 = n0 + nd;
+    if (nd == 0) return CDL_OK;
+    if (n1 > D.raw.cap) {
+      DCols grown;
+      if (!alloc_cols(grown, R.arity, std::max<uint64_t>(2 * n1, D.raw.cap * 2)))
+        return fail(CDL_E_NOMEM, "decomposed rows");
+      for (uint32_t k = 0; k < R.arity; ++k) {
+        cudaError_t e = cudaMemcpyAsync(grown.c[k], D.raw.c[k], n0 * 4, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "decomposed rows");
+      }
+      D.raw = std::move(grown);
+    }
+    for (uint32_t k = 0; k < R.arity; ++k) {
+      cudaError_t e = cudaMemcpyAsync(D.raw.c[k] + n0, R.delta.c[k], nd * 4,
+                                      cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "decomposed rows");
+    }
+    D.raw.n = n1;
+    if (opt.dedup == 2) {
+      if (n1 > D.mm_slots / 2) return dsm_multimap(R, D.raw.cap);
+      cudaError_t e = mm_insert(ctx, R.delta.c[0], nd, (uint32_t)n0, static_cast<uint2*>(D.mm.p),
+                                D.mm_slots);
+      return e == cudaSuccess ? CDL_OK : cuda_fail(e, "multimap");
+    }
+    for (uint32_t k = 0; k < R.arity; ++k) {
+      DCols add, merged, unused;
+      cdl_status r = dsm_entries(R, R.delta, k, n0, add);
+      if (r != CDL_OK) return r;
+      if (!alloc_cols(merged, 2, n1) || !alloc_cols(unused, 2, nd))
+        return fail(CDL_E_NOMEM, "index merge");
+      DBuf ws = alloc(diff_merge_workspace(n0, nd));
+      if (!ws.p) return fail(CDL_E_NOMEM, "index merge");
+      // ids are distinct, so no entry repeats: the merge keeps them all
+      cudaError_t e = diff_merge(ctx, 2, D.idx[k].in(), n0, add.in(), nd, unused.out(),
+                                 merged.out(), dslot(kSlotScratch), ws.p);
+      if (e != cudaSuccess) return cuda_fail(e, "index merge");
+      merged.n = n1;
+      D.idx[k] = std::move(merged);
+    }
+    return dsm_tables(R);
+  }
+
+  // At the end of the run Full goes back to sorted rows (what export and
+  // checkpoints read): the rows sorted lexicographically.
+  cdl_status dsm_finish() {
+    for (auto& rp : rels) {
+      Relation& R = *rp;
+      if (!R.dsm.on || !R.dsm.init) continue;
+      DCols rows;
+      const uint64_t n = R.dsm.raw.n;
+      if (!alloc_cols(rows, R.arity, n)) return fail(CDL_E_NOMEM, "sorted rows");
+      for (uint32_t k = 0; k < R.arity && n; ++k) {
+        cudaError_t e = cudaMemcpyAsync(rows.c[k], R.dsm.raw.c[k], n * 4, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "sorted rows");
+      }
+      rows.n = n;
+      uint32_t bits[kMaxK];
+      for (uint32_t k = 0; k < R.arity; ++k) bits[k] = bits_of(R.bound[k]);
+      cdl_status r = sort_cols(rows, bits);
+      if (r != CDL_OK) return r;
+      R.full = std::move(rows);
+      R.version[kFull]++;
+      R.dsm.reset();
+      R.dsm.on = true;  // stays marked: the run used the decomposed form
+    }
     return CDL_OK;
   }
 
@@ -1729,6 +1971,8 @@ struct cdl_engine {
   // atom, every other atom is an input relation joined through its hash
   // index, and every derived relation is the head of a recorded chain.
   bool graph_plan() {
+    for (auto& r : rels)
+      if (r->dsm.on) return false;  // the captured round is the merge form
     if (grec_bad || grec.empty() || opt.estimator) return false;
     std::vector<bool> active(rels.size(), false);
     for (size_t ri = 0; ri < rules.size(); ++ri) {
@@ -2050,6 +2294,7 @@ struct cdl_engine {
     propagate_bounds();
     cdl_status ds = setup_dense();
     if (ds != CDL_OK) return ds;
+    dsm_select();
     prof.reset();
     joins = 0;
     cudaEvent_t t0, t1;
@@ -2161,7 +2406,13 @@ struct cdl_engine {
         const uint64_t nd = merged[i] ? h_ctl[kSlotDelta + i] : 0;
         R.delta.n = nd;
         R.full.n += nd;
-        if (merged[i]) prof.add_bytes(kDiffMerge, 8.0 * R.arity * nd);
+        if (merged[i] && R.dsm.on) {
+          prof.add_bytes(kDedup, 4.0 * R.arity * nd);  // delta written by the compaction
+          status = dsm_append(R);
+          if (status != CDL_OK) break;
+        } else if (merged[i]) {
+          prof.add_bytes(kDiffMerge, 8.0 * R.arity * nd);
+        }
         new_total += nd;
         if (opt.n_instances && nd) {  // batched: instances that derived in this round
           cudaError_t e = mark_instances(ctx, R.delta.c[0], nd, opt.n_instances,
@@ -2199,6 +2450,10 @@ struct cdl_engine {
       }
     }
     graph_release();
+    if (status == CDL_OK || status == CDL_E_MAXITER) {
+      const cdl_status fs = dsm_finish();
+      if (status == CDL_OK) status = fs;
+    }
     if (opt.n_instances && status == CDL_OK) status = assemble();
     last_rounds = rounds;
     last_iters = iterations;
@@ -2570,6 +2825,7 @@ cdl_status cdl_create(const cdl_options* opts, cdl_engine** out) {
   auto e = std::make_unique<cdl_engine>();
   if (opts) e->opt = *opts;
   else cdl_options_default(&e->opt);
+  if (e->opt.dedup < 0 || e->opt.dedup > 2) return CDL_E_INVALID;
   e->st = static_cast<cudaStream_t>(e->opt.stream);
   e->pool.af = e->opt.alloc;
   e->pool.ff = e->opt.free;

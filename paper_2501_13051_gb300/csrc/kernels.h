@@ -29,6 +29,7 @@ enum KernelClass : int {
   kJoinDirect,
   kRetire,
   kDense,
+  kDedup,
   kNumClasses
 };
 const char* kernel_class_name(int c);
@@ -186,6 +187,34 @@ cudaError_t radix_sort(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint
                        bool* in_b, const uint64_t* dn = nullptr);
 // Column maxima into d_max[k] (for plans of unknown data).
 cudaError_t column_max(Ctx& c, ColsIn in, uint32_t k, uint64_t n, uint32_t* d_max);
+
+// ------------------------------------------------------- Algorithm 2 dedup
+// Full in the decomposed storage model: raw columns in insertion order (row
+// = surrogate id); per column k the ids in (value, id) order and the unique
+// hashmap over that order (hybrid index), or, hash-only, one multimap of
+// (value, id) entries of column 0 (packed as value | id << 32; empty = all
+// ones).
+struct DsmView {
+  ColsIn raw;
+  uint64_t n = 0;
+  const uint32_t* ids[kMaxK] = {nullptr, nullptr, nullptr, nullptr};
+  const Slot* table[kMaxK] = {nullptr, nullptr, nullptr, nullptr};
+  uint64_t mask[kMaxK] = {0, 0, 0, 0};
+  const uint2* mm = nullptr;
+  uint64_t mm_mask = 0;
+};
+// flags[i] = 1 when sorted row i repeats neither its predecessor nor a row
+// of Full (Algorithm 2), else 0.
+cudaError_t dsm_probe(Ctx& c, uint32_t k, ColsIn rows, uint64_t n, const DsmView& v,
+                      bool hash_only, uint32_t* flags);
+// out[off[i]] = rows[i] where flags[i] (off: exclusive scan of flags).
+cudaError_t compact_rows(Ctx& c, uint32_t k, ColsIn rows, uint64_t n, const uint32_t* flags,
+                         const uint64_t* off, ColsOut out);
+// Inserts (keys[i], id0 + i) into the multimap (slots a power of two).
+cudaError_t mm_insert(Ctx& c, const uint32_t* keys, uint64_t n, uint32_t id0, uint2* table,
+                      uint64_t slots);
+// out[i] = first + i.
+cudaError_t iota_u32(Ctx& c, uint32_t* out, uint64_t n, uint32_t first);
 
 // ------------------------------------------------------------------ setops
 size_t diff_merge_workspace(uint64_t n_full, uint64_t n_fresh);

@@ -7,7 +7,7 @@ const char* kernel_class_name(int c) {
   static const char* names[kNumClasses] = {
       "hash_build", "count_heads", "join_count", "scan",      "join_write", "radix_upsweep",
       "radix_scatter", "diff_count", "diff_merge", "select", "misc",
-      "estimator", "join_direct", "retire", "dense"};
+      "estimator", "join_direct", "retire", "dense", "dedup"};
   return (c >= 0 && c < kNumClasses) ? names[c] : "?";
 }
 

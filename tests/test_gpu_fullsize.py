@@ -238,13 +238,14 @@ def test_owl_rl_20m_matches_oracle(env, form):
         check_against_golden(g, st, export_all(e, prog), relation_digest)
 
 
-@pytest.mark.parametrize("form", ["plain", "graph"])
+@pytest.mark.parametrize("form", ["plain", "graph", "alg2", "alg2-hash"])
 def test_sg_forest_50k_matches_oracle(env, form):
     torch, cdl = env
     from oracle.golden import SPECS, make_program, relation_digest
     g = load_golden("sg-forest-50k")
     prog = make_program(SPECS["sg-forest-50k"])
-    with cdl.Engine(graph=(form == "graph")) as e:
+    opts = {"graph": dict(graph=True), "alg2": dict(dedup=1), "alg2-hash": dict(dedup=2)}
+    with cdl.Engine(**opts.get(form, {})) as e:
         e.load_program(prog)
         st = e.run()
         check_against_golden(g, st, export_all(e, prog), relation_digest)
