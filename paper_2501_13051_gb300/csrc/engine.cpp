@@ -945,6 +945,12 @@ struct cdl_engine {
   // --------------------------------------------------------- fresh buffers
   cdl_status ensure_fresh(Relation& r, uint64_t extra) {
     const uint64_t need = r.fresh_ub + extra;
+    // a round's new rows are sorted and merged with 32-bit row counts: the
+    // exact count of a join (or a bound on it) past that stops the run
+    // before anything is allocated or written
+    if (need > 0xFFFFFFFFull)
+      return fail(CDL_E_CAPACITY, "relation " + r.name + " would receive more than 2^32 new "
+                                  "tuples in one round");
     if (need <= r.fresh.cap && r.fresh.buf.p) {
       r.fresh_ub = need;
       return CDL_OK;
