@@ -58,15 +58,18 @@ WORKLOADS = {
                            desc="same-generation on a random forest, 200000 nodes, "
                                 "p_parent 0.98, +2% cross edges",
                            sample=dict(kind="sg", n=10_000, seed=2)),
-    "tc-er-1000-1500": dict(kind="tc", n=1000, m=1500, seed=1, graph=True,
+    "tc-er-1000-1500": dict(kind="tc", n=1000, m=1500, seed=1, graph=True, rows_also=True,
                             desc="transitive closure on a directed Erdos-Renyi graph, "
                                  "1000 nodes, 1500 edges; rounds after the first semi-naive "
                                  "one captured as one CUDA graph with a device-side loop",
                             sample=dict(kind="tc", n=1000, m=1500, seed=1)),
-    "points-to": dict(kind="pt", scale=1 / 512, seed=3, learned=True,
+    "points-to": dict(kind="pt", scale=1 / 32, seed=3, learned=True, base=dict(dense_bits=34),
                       desc="points-to analysis (valueFlow / memoryAlias / valueAlias), "
-                           "Zipf(1.1) endpoints, 2M vars / 4M assign / 1M deref times scale; "
-                           "learned join-size estimator on, exact count pass as fallback",
+                           "Zipf(1.1) endpoints, 2M vars / 4M assign / 1M deref times scale "
+                           "(2^-5: the largest power-of-two scale that fits; the full size "
+                           "stops with CDL_E_CAPACITY); new tuples of a round as bitmaps of "
+                           "tuple spaces up to 2^34; learned join-size estimator on, exact "
+                           "count pass as fallback",
                       sample=dict(kind="pt", scale=1 / 1024, seed=3),
                       train=dict(kind="pt", scale=1 / 1024, seed=103)),
     "owl-rl-20m": dict(kind="owl", triples=20_000_000, seed=4, learned=True,
@@ -112,7 +115,7 @@ def train_estimator(spec, seed_offset=0):
     t0 = time.time()
     prog = make_program(spec["train"], seed_offset)
     ninst = spec["train"]["count"] if spec["kind"] == "batch" else 0
-    with cdl.Engine(estimator=2, n_instances=ninst) as e:
+    with cdl.Engine(estimator=2, n_instances=ninst, **spec.get("base", {})) as e:
         e.load_program(prog)
         e.run()
         X, y = e.estimator_log()
@@ -332,6 +335,8 @@ def bench_gb300(args, rank, world, dist):
         form.update(autotune=1, tune_cache=cache)
     if spec.get("graph"):
         form.update(graph=True)
+    if args.dedup:
+        form.update(dedup=args.dedup)
     trained = None
     if spec.get("learned"):
         params, nsamp, tsec = train_estimator(spec, rank)
@@ -339,8 +344,11 @@ def bench_gb300(args, rank, world, dist):
         trained = {"samples": nsamp, "seconds": round(tsec, 2),
                    "instance": describe_sample(spec["train"], 0, 0).split(":")[0]}
 
-    def step(timing, plain=False):
-        with cdl.Engine(timing=timing, n_instances=ninst, **({} if plain else form)) as e:
+    base = spec.get("base", {})  # options of every form (the workload's size needs them)
+
+    def step(timing, plain=False, extra=None):
+        opts = dict(base, **(extra or ({} if plain else form)))
+        with cdl.Engine(timing=timing, n_instances=ninst, **opts) as e:
             declare(e)
             e.load_many(dev_edb)  # one check of every relation's values
             rules(e)
@@ -410,11 +418,29 @@ def bench_gb300(args, rank, world, dist):
         psecs = p0.elapsed_time(p1) * 1e-3
         plain = {"tuples_per_s": pd / psecs, "ms_per_step": 1e3 * psecs / args.steps}
 
+    # ---- the round's new tuples as sorted rows (radix sort + unique) instead
+    # of bitmaps, where the bitmap form is the default: timed the same way
+    rows = None
+    if spec.get("rows_also"):
+        torch.cuda.synchronize()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record()
+        rd = 0
+        for i in range(args.steps):
+            if i:
+                flush.fill_(i & 0xFF)
+            rd += step(False, extra=dict(form, dense_bits=-1))[0].derived_tuples
+        r1.record()
+        torch.cuda.synchronize()
+        rsecs = r0.elapsed_time(r1) * 1e-3
+        rows = {"tuples_per_s": rd / rsecs, "ms_per_step": 1e3 * rsecs / args.steps,
+                "form": "new tuples as sorted rows (LSD radix sort, unique folded into step d)"}
+
     # ---- end to end through the C ABI with host buffers
     pinned_in = {nm: [torch.from_numpy(c.view(np.int32)).pin_memory() for c in cols]
                  for nm, cols in host_cols.items()}
     sizes = {}
-    with cdl.Engine(n_instances=ninst, **form) as e:
+    with cdl.Engine(n_instances=ninst, **base, **form) as e:
         declare(e)
         e.load_many(dev_edb)  # one check of every relation's values
         rules(e)
@@ -424,7 +450,7 @@ def bench_gb300(args, rank, world, dist):
                        for _ in range(prog.arity[nm])] for nm in idb}
 
     def step_e2e():
-        with cdl.Engine(n_instances=ninst, **form) as e:
+        with cdl.Engine(n_instances=ninst, **base, **form) as e:
             declare(e)
             e.load_many(pinned_in)  # one check of every relation's values
             rules(e)
@@ -483,6 +509,14 @@ def bench_gb300(args, rank, world, dist):
         config["autotune"] = "6 tuning runs (untimed), then the cached choices"
     if spec.get("graph"):
         config["graph"] = "rounds 3.. as one CUDA graph (conditional while node)"
+    if args.dedup:
+        config["dedup"] = ("Algorithm 2, hybrid index (decomposed Full: per-column sorted ids "
+                           "+ unique hashmap)" if args.dedup == 1 else
+                           "Algorithm 2, hash-only index (multimap of column 0)")
+    if rows is not None:
+        config["rows_form"] = rows
+    if base:
+        config["options"] = base
     if plain is not None:
         config["plain_exact"] = plain
         config["form_over_plain_exact"] = value / plain["tuples_per_s"]
@@ -515,6 +549,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sg-forest-200k", choices=sorted(WORKLOADS))
     ap.add_argument("--scale", type=float, default=None, help="points-to scale factor")
+    ap.add_argument("--dedup", type=int, default=0, choices=[0, 1, 2],
+                    help="step (d): 0 merge of sorted rows, 1 Algorithm 2 (hybrid index), "
+                         "2 Algorithm 2 (hash-only index)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

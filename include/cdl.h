@@ -138,6 +138,13 @@ typedef struct {
                            the alternative Section 3 argues against.  Full is sorted back
                            into rows when the run ends.  No graph rounds with 1 or 2.
                            Results never depend on it */
+  double plan_launch_bytes; /* with the estimator on, the first join of a rule variant builds
+                           on the side that moves fewer bytes: the build side's index (none
+                           when cached; a derived relation's Full on non-leading columns
+                           priced at the incremental merge it reaches from its second round)
+                           plus 60 bytes per probe row, each launch or host wait of an index
+                           build priced as this many bytes; 0 = default 2e7 (~3 us of HBM
+                           traffic).  Results never depend on it */
 } cdl_options;
 
 /* Fills *opts with the defaults (everything zero / NULL except the
@@ -217,6 +224,10 @@ typedef struct {
   uint64_t graph_rounds;  /* options.graph: rounds run by the captured graph's device loop */
   uint64_t graph_builds;  /* options.graph: graphs captured (one more after each round that
                              outgrew the graph's buffers) */
+  uint64_t index_merges;  /* indexes of a derived relation's Full sorted by non-leading key
+                             columns that were updated by merging the round's delta into the
+                             previous version's index (Section 3's sorted indices kept
+                             incrementally) instead of sorting Full again */
 } cdl_stats;
 
 /* Runs the semi-naive loop to the fixpoint on the engine's stream and waits

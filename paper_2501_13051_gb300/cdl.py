@@ -45,7 +45,8 @@ class Options(ctypes.Structure):
                 ("n_instances", ctypes.c_uint32), ("retire", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("tune_cache", ctypes.c_char_p),
                 ("est_min_rows", ctypes.c_uint64), ("graph", ctypes.c_int32),
-                ("dense_bits", ctypes.c_int32), ("dedup", ctypes.c_int32)]
+                ("dense_bits", ctypes.c_int32), ("dedup", ctypes.c_int32),
+                ("plan_launch_bytes", ctypes.c_double)]
 
 MLP_IN = 16
 MLP_PARAMS = 5313
@@ -74,7 +75,8 @@ class Stats(ctypes.Structure):
                 ("delta_per_round", ctypes.POINTER(ctypes.c_uint64)),
                 ("delta_cap", ctypes.c_uint64),
                 ("iters_per_instance", ctypes.POINTER(ctypes.c_uint64)),
-                ("graph_rounds", ctypes.c_uint64), ("graph_builds", ctypes.c_uint64)]
+                ("graph_rounds", ctypes.c_uint64), ("graph_builds", ctypes.c_uint64),
+                ("index_merges", ctypes.c_uint64)]
 
 
 class ColRef(ctypes.Structure):
@@ -207,6 +209,7 @@ class RunStats:
     iters_per_instance: list = field(default_factory=list)
     graph_rounds: int = 0
     graph_builds: int = 0
+    index_merges: int = 0
 
 
 # kernel classes in cdl_kernel_profile order
@@ -236,7 +239,8 @@ class Engine:
     def __init__(self, *, device=None, stream=None, mem_limit=0, max_iters=0, spin_limit=0,
                  timing=False, hash_load=0.5, radix_bits=0, torch_alloc=True, estimator=0,
                  est_margin=1.0, est_params=None, n_instances=0, retire=True, autotune=0,
-                 tune_cache=None, graph=False, est_min_rows=0, dense_bits=0, dedup=0):
+                 tune_cache=None, graph=False, est_min_rows=0, dense_bits=0, dedup=0,
+                 plan_launch_bytes=0.0):
         torch = _torch()
         L = lib()
         self._L = L
@@ -264,6 +268,7 @@ class Engine:
         opts.est_min_rows = est_min_rows
         opts.dense_bits = dense_bits  # 0 default (28), -1 never
         opts.dedup = dedup  # 0 merge of sorted rows, 1 Algorithm 2 (hybrid index), 2 hash-only
+        opts.plan_launch_bytes = plan_launch_bytes
         opts.tune_cache = os.fsencode(tune_cache) if tune_cache else None
         self.n_instances = n_instances
         self._opts = opts
@@ -394,7 +399,7 @@ class Engine:
                         st.joins, st.kernel_launches, [int(buf[i]) for i in range(min(st.rounds, cap))],
                         st.est_predictions, st.est_overflows,
                         [int(inst[i]) for i in range(self.n_instances)],
-                        st.graph_rounds, st.graph_builds)
+                        st.graph_rounds, st.graph_builds, st.index_merges)
 
     # ---------------------------------------------------------- estimator
     def estimator_log(self):

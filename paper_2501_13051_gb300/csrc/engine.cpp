@@ -284,6 +284,7 @@ struct Relation {
   bool fresh_overflow = false;  // a predicted join of this round claimed past fresh.cap
   uint32_t bound[kMaxK] = {0, 0, 0, 0};  // every value of column k is <= bound[k]
   uint64_t version[2] = {1, 1};
+  uint64_t delta_version = 0;  // the Full version the last merge made: Full = previous Full + delta
   // batched runs: the rows of instances that reached their fixpoint leave
   // full for this buffer (instance i: ret_cnt[i] rows from ret_off[i])
   DCols retired;
@@ -372,6 +373,11 @@ struct cdl_engine {
   DBuf ctl;
   uint64_t* h_ctl = nullptr;
   std::vector<std::unique_ptr<Index>> cache;
+  // indexes of a Full version sorted by non-leading key columns, kept one
+  // round past their version: the next version's index is this one merged
+  // with the round's delta (incremental maintenance) instead of a new sort
+  std::vector<std::unique_ptr<Index>> prev_full;
+  uint64_t index_merges = 0;
   uint32_t radix_bits = 0;  // digit width 8, 9 or 10; 0: 8, or 9 where that saves a pass
   uint32_t digits_for(uint32_t total_bits) const {
     return radix_bits ? radix_bits : fit_digit_bits(total_bits, 8);
@@ -652,6 +658,7 @@ struct cdl_engine {
     merged.n = r.full.n;  // grows by |delta| once it is read back
     r.full = std::move(merged);
     r.version[kFull]++;
+    r.delta_version = r.version[kFull];
     if (delta_out) *delta_out = std::move(delta);
     return CDL_OK;
   }
@@ -893,17 +900,53 @@ struct cdl_engine {
       std::vector<uint32_t> perm = key;
       for (uint32_t c = 0; c < s.k; ++c)
         if (std::find(key.begin(), key.end(), c) == key.end()) perm.push_back(c);
-      if (!alloc_cols(ix->sorted, s.k, s.n)) return fail(CDL_E_NOMEM, "index copy");
-      ix->sorted.n = s.n;
       uint32_t pbits[kMaxK];
-      for (uint32_t i = 0; i < s.k; ++i) {
-        cudaError_t e = cudaMemcpyAsync(ix->sorted.c[i], s.c[perm[i]], s.n * 4,
-                                        cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return cuda_fail(e, "index copy");
-        pbits[i] = s.bits[perm[i]];
+      for (uint32_t i = 0; i < s.k; ++i) pbits[i] = s.bits[perm[i]];
+      Index* prev = nullptr;
+      if (cacheable && s.ver == kFull) {
+        const Relation& R = *rels[s.rel];
+        for (auto& p : prev_full)
+          if (p->rel == s.rel && p->key == key && p->version + 1 == R.version[kFull] &&
+              R.delta_version == R.version[kFull] && p->n + R.delta.n == s.n)
+            prev = p.get();
       }
-      cdl_status r = sort_cols(ix->sorted, pbits);
-      if (r != CDL_OK) return r;
+      if (prev) {  // previous version's sorted copy merged with the round's delta
+        const Relation& R = *rels[s.rel];
+        const uint64_t nd = R.delta.n;
+        DCols dp, unused;
+        if (!alloc_cols(dp, s.k, nd) || !alloc_cols(unused, s.k, nd) ||
+            !alloc_cols(ix->sorted, s.k, s.n))
+          return fail(CDL_E_NOMEM, "index merge");
+        dp.n = nd;
+        for (uint32_t i = 0; i < s.k && nd; ++i) {
+          cudaError_t e = cudaMemcpyAsync(dp.c[i], R.delta.c[perm[i]], nd * 4,
+                                          cudaMemcpyDeviceToDevice, st);
+          if (e != cudaSuccess) return cuda_fail(e, "index merge");
+        }
+        cdl_status r = sort_cols(dp, pbits);
+        if (r != CDL_OK) return r;
+        DBuf ws = alloc(diff_merge_workspace(prev->n, nd));
+        if (!ws.p) return fail(CDL_E_NOMEM, "index merge");
+        // delta and the previous Full share no tuple: the merge keeps them all
+        cudaError_t e = diff_merge(ctx, s.k, prev->sorted.in(), prev->n, dp.in(), nd,
+                                   unused.out(), ix->sorted.out(), dslot(kSlotScratch), ws.p);
+        if (e != cudaSuccess) return cuda_fail(e, "index merge");
+        ix->sorted.n = s.n;
+        ++index_merges;
+        prev_full.erase(std::remove_if(prev_full.begin(), prev_full.end(),
+                                       [&](const std::unique_ptr<Index>& p) { return p.get() == prev; }),
+                        prev_full.end());
+      } else {
+        if (!alloc_cols(ix->sorted, s.k, s.n)) return fail(CDL_E_NOMEM, "index copy");
+        ix->sorted.n = s.n;
+        for (uint32_t i = 0; i < s.k; ++i) {
+          cudaError_t e = cudaMemcpyAsync(ix->sorted.c[i], s.c[perm[i]], s.n * 4,
+                                          cudaMemcpyDeviceToDevice, st);
+          if (e != cudaSuccess) return cuda_fail(e, "index copy");
+        }
+        cdl_status r = sort_cols(ix->sorted, pbits);
+        if (r != CDL_OK) return r;
+      }
       for (uint32_t i = 0; i < s.k; ++i) ix->cols[perm[i]] = ix->sorted.c[i];
     }
     const uint32_t* k0 = ix->cols[key[0]];
@@ -935,9 +978,29 @@ struct cdl_engine {
   }
 
   void evict_stale() {
+    // a Full index one version behind, sorted by non-leading columns, waits
+    // for the next version's index (at most one per relation and key)
+    prev_full.erase(std::remove_if(prev_full.begin(), prev_full.end(),
+                                   [&](const std::unique_ptr<Index>& p) {
+                                     return p->version + 1 < rels[p->rel]->version[kFull];
+                                   }),
+                    prev_full.end());
+    for (auto& ix : cache) {
+      const Relation& R = *rels[ix->rel];
+      if (ix->version == R.version[ix->ver] || ix->ver != kFull || !ix->sorted.buf.p ||
+          ix->version + 1 != R.version[kFull])
+        continue;
+      prev_full.erase(std::remove_if(prev_full.begin(), prev_full.end(),
+                                     [&](const std::unique_ptr<Index>& p) {
+                                       return p->rel == ix->rel && p->key == ix->key;
+                                     }),
+                      prev_full.end());
+      ix->table.reset();  // only the sorted copy is merged
+      prev_full.push_back(std::move(ix));
+    }
     cache.erase(std::remove_if(cache.begin(), cache.end(),
                                [&](const std::unique_ptr<Index>& ix) {
-                                 return ix->version != rels[ix->rel]->version[ix->ver];
+                                 return !ix || ix->version != rels[ix->rel]->version[ix->ver];
                                }),
                 cache.end());
   }
@@ -1132,6 +1195,55 @@ struct cdl_engine {
   // hash joins starting at atom `start` (the delta atom of the variant).
   // Variable-free atoms only gate the rule; atoms that share no variable
   // with the chain so far join as a cross product.
+  // The index of a relation version on key columns is cached.
+  bool index_cached(const Src& B, const std::vector<uint32_t>& key) const {
+    if (B.rel < 0) return false;
+    const uint64_t v = rels[B.rel]->version[B.ver];
+    for (auto& ix : cache)
+      if (ix && ix->rel == B.rel && ix->ver == B.ver && ix->version == v && ix->key == key)
+        return true;
+    return false;
+  }
+  // The previous Full version's index on key waits to be merged with delta.
+  bool index_incremental(const Src& B, const std::vector<uint32_t>& key) const {
+    if (B.rel < 0 || B.ver != kFull) return false;
+    const Relation& R = *rels[B.rel];
+    for (auto& p : prev_full)
+      if (p->rel == B.rel && p->key == key && p->version + 1 == R.version[kFull] &&
+          R.delta_version == R.version[kFull])
+        return true;
+    return false;
+  }
+  // Bytes a first join moves with B as its build side and P probing it:
+  // B's index (nothing when cached; otherwise the distinct-key count and
+  // the hash build, plus, for a key that is not B's leading columns, the
+  // previous version's sorted copy merged with delta where that exists or
+  // a copy sorted in about five radix passes; a derived relation's Full is
+  // priced at the merge, which it reaches from its second round) and the
+  // probe side's count and write passes (24 + 36 bytes per probe row).  The
+  // output is the same either way.
+  double orient_bytes(const Src& B, const Src& P) const {
+    std::vector<uint32_t> key;
+    for (uint32_t bc = 0; bc < B.vars.size() && key.size() < 2; ++bc)
+      if (std::find(P.vars.begin(), P.vars.end(), B.vars[bc]) != P.vars.end()) key.push_back(bc);
+    const double n = (double)B.n, k = (double)B.k;
+    // a launch (or a host wait) priced as the bytes HBM moves meanwhile, ~3 us
+    const double kLaunch = opt.plan_launch_bytes > 0.0 ? opt.plan_launch_bytes : 2e7;
+    double idx = 0.0;
+    if (!key.empty() && !index_cached(B, key)) {
+      bool prefix = true;
+      for (size_t i = 0; i < key.size(); ++i) prefix &= key[i] == i;
+      // distinct-key count (with its read-back) and hash build: ~8 launches
+      idx = 8.0 * n * (double)key.size() + 4.0 * n + 8.0 * kLaunch;
+      // a derived relation's Full is sorted once, then merged with each
+      // round's delta: priced at that steady rate
+      const bool kept = index_incremental(B, key) ||
+                        (B.rel >= 0 && B.ver == kFull && rels[B.rel]->idb);
+      if (!prefix) idx += (kept ? 8.0 * k * n : 4.0 * k * n * 12.0) + 16.0 * kLaunch;
+    }
+    return idx + 60.0 * (double)P.n;
+  }
+
   cdl_status eval_join(const RuleR& rule, const std::vector<int>& vers, size_t start) {
     const size_t nb_all = rule.body.size();
     std::vector<Src> atoms(nb_all);
@@ -1186,6 +1298,9 @@ struct cdl_engine {
         const bool right_static = right.rel >= 0 && !rels[right.rel]->idb;
         const bool left_static = left.rel >= 0 && !rels[left.rel]->idb;
         if (!right_static && (left_static || left.n < right.n)) build_right = false;
+        // the learned form: the orientation that moves fewer bytes
+        if (opt.estimator >= 1 && !recording && !left.vars.empty() && !right.vars.empty())
+          build_right = orient_bytes(right, left) <= orient_bytes(left, right);
       }
       Src& P = build_right ? left : right;
       Src& B = build_right ? right : left;
@@ -2303,6 +2418,7 @@ struct cdl_engine {
     dsm_select();
     prof.reset();
     joins = 0;
+    index_merges = 0;
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
@@ -2456,6 +2572,7 @@ struct cdl_engine {
       }
     }
     graph_release();
+    prev_full.clear();
     if (status == CDL_OK || status == CDL_E_MAXITER) {
       const cdl_status fs = dsm_finish();
       if (status == CDL_OK) status = fs;
@@ -2493,6 +2610,7 @@ struct cdl_engine {
       stats->est_overflows = est_over;
       stats->graph_rounds = g_rounds;
       stats->graph_builds = g_builds;
+      stats->index_merges = index_merges;
       if (stats->delta_per_round)
         for (uint64_t i = 0; i < per_round.size() && i < stats->delta_cap; ++i)
           stats->delta_per_round[i] = per_round[i];

@@ -121,7 +121,7 @@ FIXPOINTS = {
 }
 
 
-def run_fixpoints(name, repeat):
+def run_fixpoints(name, repeat, **opts):
     import time
 
     import torch
@@ -135,7 +135,7 @@ def run_fixpoints(name, repeat):
     for i in range(repeat):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        with cdl.Engine() as e:
+        with cdl.Engine(**opts) as e:
             for nm, ar in prog.arity.items():
                 e.relation(nm, ar)
             e.load_many(dev)
@@ -143,7 +143,8 @@ def run_fixpoints(name, repeat):
                 e.rule(r.head, r.body, r.neq)
             st = e.run()
         torch.cuda.synchronize()
-        print(json.dumps({"fixpoint": name, "run": i, "ms": (time.perf_counter() - t) * 1e3,
+        print(json.dumps({"fixpoint": name, "opts": opts, "run": i,
+                          "ms": (time.perf_counter() - t) * 1e3,
                           "iterations": st.iterations, "derived": st.derived_tuples,
                           "kernel_launches": st.kernel_launches}), flush=True)
 
@@ -157,9 +158,11 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "zipf"])
     ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--dedup", type=int, default=0, choices=[0, 1, 2],
+                    help="fixpoints: step (d) as merge (0) or Algorithm 2 (1 hybrid, 2 hash-only)")
     args = ap.parse_args()
     if args.fixpoint:
-        run_fixpoints(args.fixpoint, args.repeat)
+        run_fixpoints(args.fixpoint, args.repeat, dedup=args.dedup)
         return
 
     import torch

@@ -46,7 +46,32 @@ def test_structs_match_header_sizes():
     assert ctypes.sizeof(cdl.Term) == 8
     assert ctypes.sizeof(cdl.ColRef) == 8
     assert ctypes.sizeof(cdl.Atom) == 16
-    assert ctypes.sizeof(cdl.Stats) == 8 * 14
+    assert ctypes.sizeof(cdl.Stats) == 8 * 15
+
+
+def test_struct_sizes_equal_the_c_compilers(tmp_path):
+    """sizeof of the ctypes mirrors equals sizeof in C for every struct of
+    the boundary (a field added to the header but not to the binding, or in
+    another order of widths, changes one of them)."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "cdl.h"\n'
+                   "int main(void) { printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(cdl_options), "
+                   "sizeof(cdl_stats), sizeof(cdl_term), sizeof(cdl_atom), sizeof(cdl_rule)); "
+                   "return 0; }\n")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    exe = tmp_path / "sizes"
+    r = subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], capture_output=True,
+                       text=True)
+    assert r.returncode == 0, r.stderr
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == [ctypes.sizeof(cdl.Options), ctypes.sizeof(cdl.Stats), ctypes.sizeof(cdl.Term),
+                   ctypes.sizeof(cdl.Atom), ctypes.sizeof(cdl.RuleS)]
 
 
 def test_header_is_plain_c(tmp_path):

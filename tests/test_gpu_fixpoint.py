@@ -273,3 +273,25 @@ def test_checkpoint_errors(cdl, tmp_path):
         with pytest.raises(cdl.CdlError) as ex:
             e.checkpoint_load(path)
         assert ex.value.name == "CDL_E_INVALID"
+
+
+@pytest.mark.parametrize("n,m,seed", [(300, 450, 4), (1000, 1500, 5)])
+def test_nonlinear_closure_merges_its_index(cdl, oracle_lib, n, m, seed):
+    """path(x, z) <- path(x, y), path(y, z).  The plain form builds on the
+    smaller side (the delta) and probes Full.  The learned form (estimator
+    on) picks the orientation that moves fewer bytes; building on Full, its
+    index on the second column is, from the second round on, the previous
+    round's index merged with the round's delta (no new sort of Full).  All
+    stay bit-exact."""
+    e = W.er_graph(n, m, seed)
+    prog = W.Program({"edge": 2, "path": 2},
+                     [W.Rule(("path", ("x", "y")), (("edge", ("x", "y")),)),
+                      W.Rule(("path", ("x", "z")), (("path", ("x", "y")), ("path", ("y", "z"))))],
+                     {"edge": e})
+    st = check(cdl, oracle_lib, prog, dense_bits=-1)
+    assert st.index_merges == 0
+    # launches priced low: at this size the byte count alone decides
+    st = check(cdl, oracle_lib, prog, dense_bits=-1, estimator=1, plan_launch_bytes=1.0)
+    assert st.index_merges > 0
+    st = check(cdl, oracle_lib, prog, dense_bits=-1, estimator=1)
+    assert st.index_merges == 0  # at the default price the small Full is probed
