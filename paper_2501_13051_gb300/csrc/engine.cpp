@@ -1215,7 +1215,8 @@ struct cdl_engine {
     return false;
   }
   // Bytes a first join moves with B as its build side and P probing it:
-  // B's index (nothing when cached; otherwise the distinct-key count and
+  // B's index (nothing when cached or when B is an input relation, whose
+  // index is built once for the run; otherwise the distinct-key count and
   // the hash build, plus, for a key that is not B's leading columns, the
   // previous version's sorted copy merged with delta where that exists or
   // a copy sorted in about five radix passes; a derived relation's Full is
@@ -1230,7 +1231,9 @@ struct cdl_engine {
     // a launch (or a host wait) priced as the bytes HBM moves meanwhile, ~3 us
     const double kLaunch = opt.plan_launch_bytes > 0.0 ? opt.plan_launch_bytes : 2e7;
     double idx = 0.0;
-    if (!key.empty() && !index_cached(B, key)) {
+    // an input relation's index is built once and kept for the whole run
+    const bool static_rel = B.rel >= 0 && !rels[B.rel]->idb;
+    if (!key.empty() && !static_rel && !index_cached(B, key)) {
       bool prefix = true;
       for (size_t i = 0; i < key.size(); ++i) prefix &= key[i] == i;
       // distinct-key count (with its read-back) and hash build: ~8 launches
