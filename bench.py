@@ -57,7 +57,10 @@ WORKLOADS = {
     "sg-forest-200k": dict(kind="sg", n=200_000, seed=2,
                            desc="same-generation on a random forest, 200000 nodes, "
                                 "p_parent 0.98, +2% cross edges",
-                           sample=dict(kind="sg", n=10_000, seed=2)),
+                           sample=dict(kind="sg", n=10_000, seed=2),
+                           learned_also=dict(est_max_rows=1 << 32),
+                           train=[dict(kind="sg", n=20_000, seed=102),
+                                  dict(kind="sg", n=60_000, seed=103)]),
     "tc-er-1000-1500": dict(kind="tc", n=1000, m=1500, seed=1, graph=True, rows_also=True,
                             desc="transitive closure on a directed Erdos-Renyi graph, "
                                  "1000 nodes, 1500 edges; rounds after the first semi-naive "
@@ -113,12 +116,17 @@ def train_estimator(spec, seed_offset=0):
     library's own kernels.  Returns (parameters, samples, seconds)."""
     from paper_2501_13051_gb300 import cdl
     t0 = time.time()
-    prog = make_program(spec["train"], seed_offset)
-    ninst = spec["train"]["count"] if spec["kind"] == "batch" else 0
-    with cdl.Engine(estimator=2, n_instances=ninst, **spec.get("base", {})) as e:
-        e.load_program(prog)
-        e.run()
-        X, y = e.estimator_log()
+    Xs, ys = [], []
+    for tr in (spec["train"] if isinstance(spec["train"], list) else [spec["train"]]):
+        prog = make_program(tr, seed_offset)
+        ninst = tr["count"] if spec["kind"] == "batch" else 0
+        with cdl.Engine(estimator=2, n_instances=ninst, **spec.get("base", {})) as e:
+            e.load_program(prog)
+            e.run()
+            Xi, yi = e.estimator_log()
+        Xs.append(Xi)
+        ys.append(yi)
+    X, y = np.concatenate(Xs), np.concatenate(ys)
     with cdl.Engine() as t:
         t.estimator_train(X, y, epochs=2000)
         params = t.estimator_params()
@@ -418,6 +426,36 @@ def bench_gb300(args, rank, world, dist):
         psecs = p0.elapsed_time(p1) * 1e-3
         plain = {"tuples_per_s": pd / psecs, "ms_per_step": 1e3 * psecs / args.steps}
 
+    # ---- the learned form beside the plain one, where the workload's own
+    # form is plain: the estimator trained first (untimed, another seed)
+    learned = None
+    if spec.get("learned_also") and not form:
+        params, nsamp, tsec = train_estimator(spec, rank)
+        lform = dict(spec["learned_also"], estimator=1, est_params=params)
+        torch.cuda.synchronize()
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record()
+        ld, lpred, lfall = 0, 0, 0
+        for i in range(args.steps):
+            if i:
+                flush.fill_(i & 0xFF)
+            lst = step(False, extra=lform)[0]
+            ld += lst.derived_tuples
+            lpred += lst.est_predictions
+            lfall += lst.est_overflows
+        l1.record()
+        torch.cuda.synchronize()
+        lsecs = l0.elapsed_time(l1) * 1e-3
+        learned = {"tuples_per_s": ld / lsecs, "ms_per_step": 1e3 * lsecs / args.steps,
+                   "over_plain": (ld / lsecs) / value,
+                   "predictions_per_step": lpred / args.steps,
+                   "fallbacks_per_step": lfall / args.steps,
+                   "trained_on": {"samples": nsamp, "seconds": round(tsec, 2),
+                                  "instances": [describe_sample(t, 0, 0).split(":")[0]
+                                                for t in spec["train"]]},
+                   "form": "learned join-size estimator (count pass skipped where predicted, "
+                           "build side by cost), exact fallback"}
+
     # ---- the round's new tuples as sorted rows (radix sort + unique) instead
     # of bitmaps, where the bitmap form is the default: timed the same way
     rows = None
@@ -513,6 +551,8 @@ def bench_gb300(args, rank, world, dist):
         config["dedup"] = ("Algorithm 2, hybrid index (decomposed Full: per-column sorted ids "
                            "+ unique hashmap)" if args.dedup == 1 else
                            "Algorithm 2, hash-only index (multimap of column 0)")
+    if learned is not None:
+        config["learned_form"] = learned
     if rows is not None:
         config["rows_form"] = rows
     if base:

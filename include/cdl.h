@@ -145,6 +145,9 @@ typedef struct {
                            plus 60 bytes per probe row, each launch or host wait of an index
                            build priced as this many bytes; 0 = default 2e7 (~3 us of HBM
                            traffic).  Results never depend on it */
+  uint64_t est_max_rows; /* predictions above this many output rows keep the exact count
+                           pass (a redo of a large join after an overflow costs more than
+                           the pass); 0 = default 2^24 */
 } cdl_options;
 
 /* Fills *opts with the defaults (everything zero / NULL except the

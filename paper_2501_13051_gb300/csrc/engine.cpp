@@ -1460,7 +1460,7 @@ struct cdl_engine {
             std::exp2(std::min(40.0, (double)h_est[kMlpIn] + est_margin + est_boost));
         // a large predicted join keeps the count pass: next to its write the
         // count is cheap, while an overflow would cost the whole round
-        if (want <= kDirectMaxTuples) {
+        if (want <= (opt.est_max_rows ? (double)opt.est_max_rows : kDirectMaxTuples)) {
           const uint64_t cap = std::max<uint64_t>(256, (uint64_t)std::ceil(want));
           Relation* H = last ? rels[rule.head.rel].get() : nullptr;
           const uint64_t cur0 = !last ? 0
