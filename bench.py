@@ -528,6 +528,16 @@ def bench_gb300(args, rank, world, dist):
                 "kernel_share": breakdown[name]["ms"] / total_ms, "launches": d["launches"],
                 "timed": "CUDA events around every launch of the kernel in the last timed step",
                 "peak_source": peak_src}
+    # step (d) as a whole: its algorithmic bytes (New and Full read, Full and
+    # delta written) over the count pass (with its tile scan) and the write
+    # pass, from the step with every class timed
+    if "diff_merge" in breakdown:
+        dm, dc = breakdown["diff_merge"], breakdown.get("diff_count", {"ms": 0.0})
+        sd = dm["bytes"] / ((dm["ms"] + dc["ms"]) * 1e-3) / 1e9
+        roofline["step_d"] = {"achieved": sd, "peak": peak, "unit": "GB/s", "frac": sd / peak,
+                              "bytes": dm["bytes"], "ms": dm["ms"] + dc["ms"],
+                              "kernels": "count pass + tile scan + write pass (diff_count, "
+                                         "diff_merge), the step with every class timed"}
     # ---- the oracle on a bounded sample, on this host's cores
     sspec = spec["sample"]
     od, osecs = run_oracle_sample(sspec)

@@ -423,12 +423,18 @@ cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, u
     k_count_new<K><<<(unsigned)count_grid, kDT, smem_count, c.st>>>(
         full, fresh, n_full, n_fresh, splits, corank, cnt, tiles, dm, (uint32_t)group);
   }
-  e = exclusive_scan(c, cnt, tiles, pre, d_ndelta, scan_ws, d_tiles);
+  {
+    const int sc = c.scan_cls;  // the tile counts' scan is timed with the count pass
+    c.scan_cls = kDiffCount;
+    e = exclusive_scan(c, cnt, tiles, pre, d_ndelta, scan_ws, d_tiles);
+    c.scan_cls = sc;
+  }
   if (e != cudaSuccess) return e;
-  // read Full, New and the co-ranks, write Full again; the delta part of the
-  // writes (merged and delta) is added once its size is known
+  // the step's algorithmic bytes: Full and New read, Full written again (the
+  // co-ranks this pass also reads are the count pass's overhead); the delta
+  // part of the writes (merged and delta) is added once its size is known
   const double mb = merged.c[0] ? 4.0 * K * n_full : 0.0;
-  ProfScope p(c, kDiffMerge, 4.0 * K * (n_full + n_fresh) + 4.0 * n_fresh + mb);
+  ProfScope p(c, kDiffMerge, 4.0 * K * (n_full + n_fresh) + mb);
   k_merge_write<K><<<(unsigned)tiles, kDT, 0, c.st>>>(full, n_full, fresh, n_fresh, splits, corank,
                                                       pre, delta, merged, dm);
   return cudaGetLastError();

@@ -64,6 +64,7 @@ struct Ctx {
   uint32_t* d_err = nullptr;
   Profiler* prof = nullptr;
   uint64_t spin_limit = 1ull << 26;
+  int scan_cls = kScan;  // the class a scan's launches are timed under (a step may own its scans)
 };
 
 struct ProfScope {

@@ -139,7 +139,7 @@ cudaError_t exclusive_scan(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
   uint64_t* sums = static_cast<uint64_t*>(ws);
   {
-    ProfScope p(c, kScan, 4.0 * n);
+    ProfScope p(c, c.scan_cls, 4.0 * n);
     k_scan_reduce<<<(unsigned)tiles, kScanThreads, 0, c.st>>>(in, n, sums, dn);
   }
   return scan_finish(c, in, n, out, d_total, ws, dn);
@@ -151,7 +151,7 @@ cudaError_t scan_finish(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out, u
     if (d_total) return cudaMemsetAsync(d_total, 0, sizeof(uint64_t), c.st);
     return cudaSuccess;
   }
-  ProfScope p(c, kScan, 4.0 * n + 8.0 * n);
+  ProfScope p(c, c.scan_cls, 4.0 * n + 8.0 * n);
   if (n <= kSmallScan) {  // tile sums, if any were stored, are not needed
     k_scan_small<<<1, kTopThreads, 0, c.st>>>(in, n, out, d_total, dn);
     return cudaGetLastError();
