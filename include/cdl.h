@@ -231,6 +231,9 @@ typedef struct {
                              columns that were updated by merging the round's delta into the
                              previous version's index (Section 3's sorted indices kept
                              incrementally) instead of sorting Full again */
+  uint64_t graph_retirements; /* batched runs with options.graph: rounds of the captured
+                             graph in which converged instances' rows left Full (decided and
+                             moved on the device) */
 } cdl_stats;
 
 /* Runs the semi-naive loop to the fixpoint on the engine's stream and waits

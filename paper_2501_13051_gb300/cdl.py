@@ -76,7 +76,7 @@ class Stats(ctypes.Structure):
                 ("delta_cap", ctypes.c_uint64),
                 ("iters_per_instance", ctypes.POINTER(ctypes.c_uint64)),
                 ("graph_rounds", ctypes.c_uint64), ("graph_builds", ctypes.c_uint64),
-                ("index_merges", ctypes.c_uint64)]
+                ("index_merges", ctypes.c_uint64), ("graph_retirements", ctypes.c_uint64)]
 
 
 class ColRef(ctypes.Structure):
@@ -210,6 +210,7 @@ class RunStats:
     graph_rounds: int = 0
     graph_builds: int = 0
     index_merges: int = 0
+    graph_retirements: int = 0
 
 
 # kernel classes in cdl_kernel_profile order
@@ -400,7 +401,8 @@ class Engine:
                         st.joins, st.kernel_launches, [int(buf[i]) for i in range(min(st.rounds, cap))],
                         st.est_predictions, st.est_overflows,
                         [int(inst[i]) for i in range(self.n_instances)],
-                        st.graph_rounds, st.graph_builds, st.index_merges)
+                        st.graph_rounds, st.graph_builds, st.index_merges,
+                        st.graph_retirements)
 
     # ---------------------------------------------------------- estimator
     def estimator_log(self):

@@ -441,6 +441,7 @@ struct cdl_engine {
   struct GRelRes {
     uint32_t rel = 0;
     DCols F[2], D[2], fresh, alt;
+    DCols ret;  // batched runs: the retired rows while the graph runs
     DBuf sort_ws, merge_ws;
     RadixPlan plan;
     bool sorted_in_alt = false;
@@ -456,6 +457,16 @@ struct cdl_engine {
   std::vector<GStepRes> gstep;
   std::vector<uint64_t> gcap_u, gcap_i, gcap_f;  // capacities by relation / step
   DBuf gdev;
+  // device-side retirement of a batched graph: RetireCtl, then the
+  // relations' RetireRel, then live / conv flags and the per-instance arrays
+  DBuf gret;
+  uint64_t gret_room = 1;  // retired buffers start at this many times Full's capacity
+  uint64_t g_retirements = 0;  // rounds whose converged rows the graph moved out of Full
+  bool graph_retires() const { return opt.n_instances && opt.retire >= 0; }
+  RetireCtl* g_rctl() const { return static_cast<RetireCtl*>(gret.p); }
+  RetireRel* g_rrel() const {
+    return reinterpret_cast<RetireRel*>(static_cast<char*>(gret.p) + 256);
+  }
   cudaGraph_t ggraph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   uint64_t glaunches_per_round = 0;
@@ -2131,6 +2142,7 @@ struct cdl_engine {
     grel.clear();
     gstep.clear();
     gdev.reset();
+    gret.reset();
   }
 
   // Device state layout inside gdev.
@@ -2210,6 +2222,10 @@ struct cdl_engine {
       S.wws = alloc(S.wbytes);
       if (!S.off.p || !S.cws.p || !S.wws.p) return fail(CDL_E_NOMEM, "graph join buffers");
       if (!g.last && !alloc_cols(S.inter, g.js.out_k, S.ocap)) return fail(CDL_E_NOMEM, "graph join buffers");
+    }
+    if (graph_retires()) {
+      cdl_status rr = graph_retire_setup();
+      if (rr != CDL_OK) return rr;
     }
     GraphCtl ctl{};
     ctl.round = rounds_done;
@@ -2319,7 +2335,100 @@ struct cdl_engine {
     if (e == cudaSuccess)
       e = round_end(ctx, g_cur(), g_next(), (uint32_t)grel.size(), g_ctl(), g_round(), kGraphRounds,
                     loop, g_cursor(0), (uint32_t)grel.size(), g_step(0, 0), (uint32_t)gstep.size());
+    if (e == cudaSuccess && graph_retires()) {
+      std::vector<uint32_t> ar(grel.size());
+      for (size_t j = 0; j < grel.size(); ++j) ar[j] = rels[grel[j].rel]->arity;
+      e = retire_round(ctx, g_cur(), g_next(), g_ctl(), g_rctl(), g_rrel(), ar.data(),
+                       (uint32_t)grel.size(), opt.n_instances,
+                       static_cast<const uint64_t*>(inst_last.p));
+    }
     return e;
+  }
+
+  // The retirement state of a batched graph: the host's flags, retired rows
+  // and per-instance places copied to the device (the graph continues them).
+  cdl_status graph_retire_setup() {
+    const uint32_t ni = opt.n_instances;
+    const size_t nrel = grel.size();
+    const size_t per_rel = 8 * (size_t)(7 * ni + 3);  // bounds, kseg, rseg (ni + 1); ret, src (ni)
+    const size_t bytes = 256 + ((sizeof(RetireRel) * nrel + 255) & ~size_t(255)) + 8 * (size_t)ni +
+                         per_rel * nrel + 256;
+    gret = alloc(bytes);
+    if (!gret.p) return fail(CDL_E_NOMEM, "graph retirement state");
+    char* base = static_cast<char*>(gret.p);
+    char* p = base + 256 + ((sizeof(RetireRel) * nrel + 255) & ~size_t(255));
+    RetireCtl rc{};
+    rc.live = reinterpret_cast<uint32_t*>(p);
+    rc.conv = rc.live + ni;
+    p += 8 * (size_t)ni;
+    std::vector<uint32_t> flags(2 * (size_t)ni);
+    for (uint32_t i = 0; i < ni; ++i) {
+      flags[i] = inst_live[i];
+      flags[ni + i] = inst_conv[i];
+    }
+    cudaError_t e = cudaMemcpyAsync(rc.live, flags.data(), 8 * (size_t)ni, cudaMemcpyHostToDevice, st);
+    std::vector<RetireRel> rr(nrel);
+    for (size_t j = 0; j < nrel && e == cudaSuccess; ++j) {
+      GRelRes& G = grel[j];
+      Relation& R = *rels[G.rel];
+      uint64_t* a = reinterpret_cast<uint64_t*>(p + per_rel * j);
+      RetireRel& q = rr[j];
+      q.bounds = a;
+      q.kseg_off = a + (ni + 1);
+      q.rseg_off = a + 2 * (size_t)(ni + 1);
+      q.ret_off = a + 3 * (size_t)(ni + 1);
+      q.ret_cnt = q.ret_off + ni;
+      q.kseg_src = q.ret_cnt + ni;
+      q.rseg_src = q.kseg_src + ni;
+      q.ret_cap = std::max<uint64_t>(2 * R.retired.n, gret_room * G.Fcap);
+      if (!alloc_cols(G.ret, R.arity, q.ret_cap)) return fail(CDL_E_NOMEM, "graph retired rows");
+      q.ret = G.ret.out();
+      q.ret_n = R.retired.n;
+      for (uint32_t k = 0; k < R.arity && R.retired.n && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(G.ret.c[k], R.retired.c[k], 4 * R.retired.n, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(q.ret_off, R.ret_off.data(), 8 * (size_t)ni, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(q.ret_cnt, R.ret_cnt.data(), 8 * (size_t)ni, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base, &rc, sizeof rc, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(base + 256, rr.data(), sizeof(RetireRel) * nrel, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors die here
+    return e == cudaSuccess ? CDL_OK : cuda_fail(e, "graph retirement state");
+  }
+
+  // The graph's retirement state back to the host (after its launch).
+  cdl_status graph_retire_collect() {
+    const uint32_t ni = opt.n_instances;
+    const size_t nrel = grel.size();
+    RetireCtl rc{};
+    std::vector<RetireRel> rr(nrel);
+    cudaError_t e = cudaMemcpyAsync(&rc, gret.p, sizeof rc, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rr.data(), g_rrel(), sizeof(RetireRel) * nrel, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "graph retirement state");
+    std::vector<uint32_t> flags(2 * (size_t)ni);
+    e = cudaMemcpy(flags.data(), rc.live, 8 * (size_t)ni, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "graph retirement state");
+    for (uint32_t i = 0; i < ni; ++i) {
+      inst_live[i] = (uint8_t)flags[i];
+      inst_conv[i] = (uint8_t)flags[ni + i];
+    }
+    if (rc.short_room) gret_room *= 2;
+    g_retirements += rc.moves;
+    for (size_t j = 0; j < nrel; ++j) {
+      GRelRes& G = grel[j];
+      Relation& R = *rels[G.rel];
+      e = cudaMemcpy(R.ret_off.data(), rr[j].ret_off, 8 * (size_t)ni, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(R.ret_cnt.data(), rr[j].ret_cnt, 8 * (size_t)ni, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e, "graph retirement state");
+      R.retired = std::move(G.ret);
+      R.retired.n = rr[j].ret_n;
+    }
+    return CDL_OK;
   }
 
   // Runs rounds on the device until the fixpoint, max_iters or a buffer
@@ -2363,6 +2472,10 @@ struct cdl_engine {
     g_rounds += ctl.round - first;
     round = ctl.round;
     iterations = ctl.iterations;
+    if (graph_retires()) {
+      r = graph_retire_collect();
+      if (r != CDL_OK) return r;
+    }
     for (size_t j = 0; j < grel.size(); ++j) {
       GRelRes& G = grel[j];
       Relation& R = *rels[G.rel];
@@ -2463,7 +2576,7 @@ struct cdl_engine {
     }
     grec.clear();
     grec_bad = graph_ready = false;
-    g_rounds = g_builds = 0;
+    g_rounds = g_builds = g_retirements = 0;
     for (uint64_t round = resume_rounds + 1; status == CDL_OK; ++round) {
       cur_round = round;
       cudaError_t e = cudaSuccess;
@@ -2614,6 +2727,7 @@ struct cdl_engine {
       stats->graph_rounds = g_rounds;
       stats->graph_builds = g_builds;
       stats->index_merges = index_merges;
+      stats->graph_retirements = g_retirements;
       if (stats->delta_per_round)
         for (uint64_t i = 0; i < per_round.size() && i < stats->delta_cap; ++i)
           stats->delta_per_round[i] = per_round[i];

@@ -295,6 +295,38 @@ cudaError_t round_end(Ctx& c, GraphRel* cur, GraphRel* next, uint32_t nrel, Grap
                       uint64_t* per_round, uint64_t per_round_cap,
                       cudaGraphConditionalHandle loop, uint64_t* cursors, uint32_t ncur,
                       uint64_t* steps, uint32_t nsteps);
+
+// Retirement of converged instances inside a captured batched round (device
+// state; retire.cu).  live[i]: instance i's rows are still in Full; conv[i]:
+// it reached its fixpoint (rows leave Full, or have left once live is 0).
+struct RetireCtl {
+  uint32_t* live;
+  uint32_t* conv;
+  uint32_t go;          // rows move this round
+  uint32_t short_room;  // a retired buffer was too small for a move
+  uint64_t moves;       // rounds whose converged rows moved out of Full
+};
+// Per derived relation: the retired rows (instance i: ret_cnt[i] rows from
+// ret_off[i]), the instances' bounds in Full, and this round's tables of
+// kept and retired segments (one per instance, ni + 1 offsets each).
+struct RetireRel {
+  ColsOut ret;
+  uint64_t ret_cap, ret_n;
+  uint64_t* bounds;
+  uint64_t* ret_off;
+  uint64_t* ret_cnt;
+  uint64_t* kseg_off;
+  uint64_t* kseg_src;
+  uint64_t* rseg_off;
+  uint64_t* rseg_src;
+  uint64_t kept, moved;
+};
+// After round_end: converged instances' rows leave cur's Full once they are
+// 1/8 of all Full rows (kept rows gathered into next's free Full buffer,
+// which then becomes cur's).  arity: host array of the nrel arities.
+cudaError_t retire_round(Ctx& c, GraphRel* cur, GraphRel* next, GraphCtl* ctl, RetireCtl* rc,
+                         RetireRel* rr, const uint32_t* arity, uint32_t nrel, uint32_t ni,
+                         const uint64_t* last_round);
 // col[j] = s for the rows j of segment s: [off[s], off[s + 1]), off having
 // nseg + 1 device entries and off[nseg] = total.
 cudaError_t fill_segments(Ctx& c, uint32_t* col, const uint64_t* off, uint32_t nseg,

@@ -251,7 +251,7 @@ def test_sg_forest_50k_matches_oracle(env, form):
         check_against_golden(g, st, export_all(e, prog), relation_digest)
 
 
-@pytest.mark.parametrize("form", ["exact", "learned+tuned"])
+@pytest.mark.parametrize("form", ["exact", "learned+tuned", "graph+tuned"])
 def test_batched_512_matches_oracle(env, form, tmp_path):
     torch, cdl = env
     from oracle.golden import relation_digest
@@ -260,19 +260,25 @@ def test_batched_512_matches_oracle(env, form, tmp_path):
     graphs, kinds = W.batched_instances(sp["count"], sp["seed"], sp["lo"], sp["hi"])
     prog = W.batched_program(graphs, kinds)
     opts = dict(n_instances=sp["count"])
-    if form == "learned+tuned":
-        bench = bench_module()
+    if form != "exact":
         cache = str(tmp_path / "tune.txt")
         with cdl.Engine(autotune=2, tune_cache=cache, **opts) as e:  # one tuning run
             e.load_program(prog)
             e.run()
+        opts.update(autotune=1, tune_cache=cache)
+    if form == "learned+tuned":
+        bench = bench_module()
         params, _, _ = bench.train_estimator(bench.WORKLOADS["batched-512"])
-        opts.update(autotune=1, tune_cache=cache, estimator=1, est_params=params)
+        opts.update(estimator=1, est_params=params)
+    if form == "graph+tuned":  # rounds in the captured graph, retirement on the device
+        opts.update(graph=True)
     with cdl.Engine(**opts) as e:
         e.load_program(prog)
         st = e.run()
         rels = {nm: e.export(nm) for nm in ("tc_path", "sg")}
     check_against_golden(g, st, rels, relation_digest)
+    if form == "graph+tuned":
+        assert st.graph_rounds > 0 and st.graph_retirements > 0
     got_n = {}
     for nm, rows in rels.items():
         got_n.update({int(i): int(c) for i, c in

@@ -71,6 +71,28 @@ def test_batched_instances_as_graph(cdl, oracle_lib):
         assert st.iters_per_instance[i] == oracle_lib.run_program(single).iterations, i
 
 
+@pytest.mark.parametrize("count,seed,lo,hi", [(64, 84, 50, 4000), (96, 85, 20, 1500)])
+def test_batched_graph_retires_on_the_device(cdl, oracle_lib, count, seed, lo, hi):
+    """Batched rounds inside the captured graph, converged instances' rows
+    moved out of Full by the device (decision, segment tables and gather):
+    every instance equal to its own oracle run, tuples and iteration count."""
+    graphs, kinds = W.batched_instances(count, seed, lo, hi)
+    prog = W.batched_program(graphs, kinds)
+    with cdl.Engine(n_instances=count, graph=True) as e:
+        e.load_program(prog)
+        st = e.run()
+        rel = {"tc": e.export("tc_path"), "sg": e.export("sg")}
+    assert st.graph_rounds > 0 and st.graph_retirements > 0
+    for i, (g, k) in enumerate(zip(graphs, kinds)):
+        single = W.tc_program(g) if k == "tc" else W.sg_program(g)
+        want = oracle_lib.run_program(single)
+        rows = rel[k]
+        assert np.array_equal(rows[rows[:, 0] == i][:, 1:],
+                              want.relations["path" if k == "tc" else "sg"]), i
+        assert st.iters_per_instance[i] == want.iterations, i
+    assert max(st.iters_per_instance) == st.iterations
+
+
 def test_programs_outside_the_graph_class_run_as_usual(cdl, oracle_lib):
     # mutually recursive rules joining derived relations with each other
     check(cdl, oracle_lib, W.points_to_program(W.points_to_edb(1 / 2048, 5)), graph=True)
