@@ -45,8 +45,8 @@
 extern "C" {
 #endif
 
-#define CDL_MAX_ARITY 4
-#define CDL_MAX_BODY 4
+#define CDL_MAX_ARITY 8
+#define CDL_MAX_BODY 8
 #define CDL_EMPTY_KEY 0xFFFFFFFFu
 
 typedef enum {

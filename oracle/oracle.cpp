@@ -37,7 +37,7 @@
 
 namespace {
 
-constexpr int kMaxArity = 4;
+constexpr int kMaxArity = 8;
 using Tuple = std::array<uint32_t, kMaxArity>;
 using Rel = std::set<Tuple>;
 

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcdl.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "cdl.h")
 
-MAX_ARITY = 4
+MAX_ARITY = 8
 STATUS = {0: "CDL_OK", -1: "CDL_E_INVALID", -2: "CDL_E_NOMEM", -3: "CDL_E_CAPACITY",
           -4: "CDL_E_VALUE", -5: "CDL_E_MAXITER", -6: "CDL_E_TIMEOUT", -7: "CDL_E_CUDA",
           -8: "CDL_E_STATE"}

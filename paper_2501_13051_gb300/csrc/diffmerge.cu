@@ -459,6 +459,10 @@ cudaError_t diff_merge(Ctx& c, uint32_t k, ColsIn full, uint64_t n_full, ColsIn 
     case 2: return run_diff_merge<2>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws, d);
     case 3: return run_diff_merge<3>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws, d);
     case 4: return run_diff_merge<4>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws, d);
+    case 5: return run_diff_merge<5>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws, d);
+    case 6: return run_diff_merge<6>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws, d);
+    case 7: return run_diff_merge<7>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws, d);
+    case 8: return run_diff_merge<8>(c, full, n_full, fresh, n_fresh, delta, merged, d_ndelta, ws, d);
     default: return cudaErrorInvalidValue;
   }
 }

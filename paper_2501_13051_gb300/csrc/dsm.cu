@@ -143,6 +143,10 @@ cudaError_t dsm_probe(Ctx& c, uint32_t k, ColsIn rows, uint64_t n, const DsmView
     case 2: return launch_probe<2>(c, rows, n, v, hash_only, flags);
     case 3: return launch_probe<3>(c, rows, n, v, hash_only, flags);
     case 4: return launch_probe<4>(c, rows, n, v, hash_only, flags);
+    case 5: return launch_probe<5>(c, rows, n, v, hash_only, flags);
+    case 6: return launch_probe<6>(c, rows, n, v, hash_only, flags);
+    case 7: return launch_probe<7>(c, rows, n, v, hash_only, flags);
+    case 8: return launch_probe<8>(c, rows, n, v, hash_only, flags);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -157,6 +161,10 @@ cudaError_t compact_rows(Ctx& c, uint32_t k, ColsIn rows, uint64_t n, const uint
     case 2: k_compact_rows<2><<<grid, kPT, 0, c.st>>>(rows, n, flags, off, out); break;
     case 3: k_compact_rows<3><<<grid, kPT, 0, c.st>>>(rows, n, flags, off, out); break;
     case 4: k_compact_rows<4><<<grid, kPT, 0, c.st>>>(rows, n, flags, off, out); break;
+    case 5: k_compact_rows<5><<<grid, kPT, 0, c.st>>>(rows, n, flags, off, out); break;
+    case 6: k_compact_rows<6><<<grid, kPT, 0, c.st>>>(rows, n, flags, off, out); break;
+    case 7: k_compact_rows<7><<<grid, kPT, 0, c.st>>>(rows, n, flags, off, out); break;
+    case 8: k_compact_rows<8><<<grid, kPT, 0, c.st>>>(rows, n, flags, off, out); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

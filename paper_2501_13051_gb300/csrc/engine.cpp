@@ -3110,7 +3110,7 @@ cdl_status cdl_destroy(cdl_engine* e) {
 cdl_status cdl_relation_create(cdl_engine* e, const char* name, uint32_t arity, cdl_rel* out) {
   if (!e || !name || !out) return CDL_E_INVALID;
   if (e->ran) return e->fail(CDL_E_STATE, "relations must precede cdl_run");
-  if (arity < 1 || arity > CDL_MAX_ARITY) return e->fail(CDL_E_INVALID, "arity must be 1..4");
+  if (arity < 1 || arity > CDL_MAX_ARITY) return e->fail(CDL_E_INVALID, "arity must be 1..8");
   if (e->by_name.count(name)) return e->fail(CDL_E_INVALID, std::string("duplicate relation ") + name);
   if (e->rels.size() >= kMaxRels) return e->fail(CDL_E_INVALID, "too many relations");
   auto r = std::make_unique<Relation>();
@@ -3141,7 +3141,7 @@ cdl_status cdl_rule_add(cdl_engine* e, const cdl_rule* rule) {
   if (!e || !rule) return CDL_E_INVALID;
   if (e->ran) return e->fail(CDL_E_STATE, "rules must precede cdl_run");
   if (rule->nbody < 1 || rule->nbody > CDL_MAX_BODY || !rule->body)
-    return e->fail(CDL_E_INVALID, "a rule needs 1..4 body atoms");
+    return e->fail(CDL_E_INVALID, "a rule needs 1..8 body atoms");
   auto conv = [&](const cdl_atom& a, AtomR& out) -> bool {
     if (a.rel >= e->rels.size() || a.arity != e->rels[a.rel]->arity || !a.terms) return false;
     out.rel = a.rel;

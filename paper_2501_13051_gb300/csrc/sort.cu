@@ -320,6 +320,10 @@ cudaError_t radix_sort(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uint
     case 2: return sort_k<2>(c, plan, a, b, n, ws, in_b, dn);
     case 3: return sort_k<3>(c, plan, a, b, n, ws, in_b, dn);
     case 4: return sort_k<4>(c, plan, a, b, n, ws, in_b, dn);
+    case 5: return sort_k<5>(c, plan, a, b, n, ws, in_b, dn);
+    case 6: return sort_k<6>(c, plan, a, b, n, ws, in_b, dn);
+    case 7: return sort_k<7>(c, plan, a, b, n, ws, in_b, dn);
+    case 8: return sort_k<8>(c, plan, a, b, n, ws, in_b, dn);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -295,3 +295,39 @@ def test_nonlinear_closure_merges_its_index(cdl, oracle_lib, n, m, seed):
     assert st.index_merges > 0
     st = check(cdl, oracle_lib, prog, dense_bits=-1, estimator=1)
     assert st.index_merges == 0  # at the default price the small Full is probed
+
+
+def wide_program(seed):
+    """Relations of arity 5 to 8 and rules of up to six body atoms (the
+    shape of TGD-style rules): paths of five edges as 6-ary tuples, 8-node
+    windows of walks that start at a node with a given attribute, slid one
+    node per round (recursive), and an attribute relation of arity 5 joined
+    on two columns with a constant and an inequality."""
+    e = W.er_graph(60, 100, seed)
+    rng = np.random.default_rng(seed)
+    attr = np.unique(np.stack([np.arange(60), rng.integers(0, 3, 60), rng.integers(0, 3, 60),
+                               rng.integers(0, 5, 60), rng.integers(0, 2, 60)],
+                              axis=1).astype(np.uint32), axis=0)
+    R = W.Rule
+    rules = [
+        R(("t6", ("a", "b", "c", "d", "f", "g")),
+          (("e", ("a", "b")), ("e", ("b", "c")), ("e", ("c", "d")), ("e", ("d", "f")),
+           ("e", ("f", "g")))),
+        R(("w8", ("a", "b", "c", "d", "f", "g", "h", "i")),
+          (("t6", ("a", "b", "c", "d", "f", "g")), ("e", ("g", "h")), ("e", ("h", "i")),
+           ("attr", ("a", 0, "p", "q", "r")))),
+        R(("w8", ("b", "c", "d", "f", "g", "h", "i", "j")),
+          (("w8", ("a", "b", "c", "d", "f", "g", "h", "i")), ("e", ("i", "j")))),
+        R(("m7", ("x", "y", "p", "q", "r", "s", 9)),
+          (("e", ("x", "y")), ("attr", ("x", "p", "q", "r", "s")), ("attr", ("y", "p", "q", "u", "v")),
+           ("e", ("y", "z")), ("attr", ("z", "p", "k", "l", "m")), ("e", ("z", "x2"))),
+          (("x", "y"),)),
+    ]
+    arity = {"e": 2, "attr": 5, "t6": 6, "w8": 8, "m7": 7}
+    return W.Program(arity, rules, {"e": e, "attr": attr})
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+@pytest.mark.parametrize("dense", [0, -1], ids=["dense", "sorted"])
+def test_wide_relations_and_long_bodies(cdl, oracle_lib, seed, dense):
+    check(cdl, oracle_lib, wide_program(seed), dense_bits=dense)
