@@ -31,9 +31,20 @@ constexpr uint32_t kDRows = 8;  // ... and the most probe rows a block walks one
 constexpr int kJItems = 8;
 constexpr int kJTile = kJT * kJItems;  // merged items per block
 
+// Column v of a column set held in registers: a chain of selects with
+// constant indices, so that a run-time column number does not send the set
+// to local memory.
+__device__ __forceinline__ const uint32_t* col_of(const ColsIn& c, uint32_t v) {
+  const uint32_t* p = c.c[0];
+#pragma unroll
+  for (int k = 1; k < kMaxK; ++k)
+    if (v == (uint32_t)k) p = c.c[k];
+  return p;
+}
+
 __device__ __forceinline__ uint32_t probe_key1(const JoinSpec& j, const ColsIn& probe,
                                               uint64_t row) {
-  return j.pk1 == 0xFFu ? 0u : __ldg(probe.c[j.pk1] + row);
+  return j.pk1 == 0xFFu ? 0u : __ldg(col_of(probe, j.pk1) + row);
 }
 
 // Range of build rows matching probe row `row`: the hybrid index lookup, or
@@ -44,7 +55,8 @@ __device__ __forceinline__ uint32_t lookup(const JoinSpec& j, const ColsIn& prob
     *start = 0;
     return j.n_build;
   }
-  return probe_table(j.table, mask, __ldg(probe.c[j.pk0] + row), probe_key1(j, probe, row), start);
+  return probe_table(j.table, mask, __ldg(col_of(probe, j.pk0) + row), probe_key1(j, probe, row),
+                     start);
 }
 
 // The probe side of a launch: the spec's columns and row count, or (inside
@@ -131,7 +143,7 @@ __global__ void k_write_splits(const uint64_t* __restrict__ off, uint64_t n, uin
 
 __device__ __forceinline__ uint32_t ref_value(const JoinSpec& j, const ColsIn& probe, const Ref& r,
                                               uint64_t row, uint64_t brow) {
-  if (r.side == 0) return __ldg(probe.c[r.v] + row);
+  if (r.side == 0) return __ldg(col_of(probe, r.v) + row);
   if (r.side == 1) return __ldg(j.build.c[r.v] + brow);
   return r.v;
 }

@@ -143,8 +143,10 @@ __global__ void __launch_bounds__(kGT) k_gather_segments(ColsIn a, ColsIn b, uin
     const uint64_t start = SMEM ? s_off[lo] : __ldg(out_off + lo);
     const uint64_t sv = __ldg(src + lo);
     const uint64_t row = (sv & ~(1ull << 63)) + (j - start);
-    const ColsIn& t = (sv >> 63) ? b : a;
-    for (uint32_t c = 0; c < k; ++c) out.c[c][j] = __ldg(t.c[c] + row);
+    const bool from_b = (sv >> 63) != 0;
+#pragma unroll
+    for (int c = 0; c < kMaxK; ++c)  // constant indices: the column sets stay in registers
+      if (c < (int)k) out.c[c][j] = __ldg((from_b ? b.c[c] : a.c[c]) + row);
   }
 }
 
