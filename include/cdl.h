@@ -148,6 +148,15 @@ typedef struct {
   uint64_t est_max_rows; /* predictions above this many output rows keep the exact count
                            pass (a redo of a large join after an overflow costs more than
                            the pass); 0 = default 2^24 */
+  int32_t host_full;    /* out-of-core relations: 1 = the Full version of derived
+                           relations whose Full no rule variant reads after round 1 (as for
+                           dedup) lives in pinned host memory; the merge of step (d) reads
+                           and writes it in place over the CPU-GPU link, so its size is
+                           bounded by host memory instead of the device's (and by
+                           mem_limit, which counts device memory only).  Exports and
+                           checkpoints read it where it is.  Not with dedup or batched
+                           runs; no graph rounds.  0 = default, Full in device memory.
+                           Results never depend on it */
 } cdl_options;
 
 /* Fills *opts with the defaults (everything zero / NULL except the

@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("tune_cache", ctypes.c_char_p),
                 ("est_min_rows", ctypes.c_uint64), ("graph", ctypes.c_int32),
                 ("dense_bits", ctypes.c_int32), ("dedup", ctypes.c_int32),
-                ("plan_launch_bytes", ctypes.c_double), ("est_max_rows", ctypes.c_uint64)]
+                ("plan_launch_bytes", ctypes.c_double), ("est_max_rows", ctypes.c_uint64),
+                ("host_full", ctypes.c_int32)]
 
 MLP_IN = 16
 MLP_PARAMS = 5313
@@ -241,7 +242,7 @@ class Engine:
                  timing=False, hash_load=0.5, radix_bits=0, torch_alloc=True, estimator=0,
                  est_margin=1.0, est_params=None, n_instances=0, retire=True, autotune=0,
                  tune_cache=None, graph=False, est_min_rows=0, dense_bits=0, dedup=0,
-                 plan_launch_bytes=0.0, est_max_rows=0):
+                 plan_launch_bytes=0.0, est_max_rows=0, host_full=0):
         torch = _torch()
         L = lib()
         self._L = L
@@ -271,6 +272,7 @@ class Engine:
         opts.dedup = dedup  # 0 merge of sorted rows, 1 Algorithm 2 (hybrid index), 2 hash-only
         opts.plan_launch_bytes = plan_launch_bytes
         opts.est_max_rows = est_max_rows
+        opts.host_full = host_full  # 1: Full of step-(d)-only relations in pinned host memory
         opts.tune_cache = os.fsencode(tune_cache) if tune_cache else None
         self.n_instances = n_instances
         self._opts = opts

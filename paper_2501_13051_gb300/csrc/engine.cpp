@@ -47,6 +47,9 @@ class Pool {
   void* ctx = nullptr;
   uint64_t limit = 0;
   uint64_t held = 0;
+  // chunks of pinned host memory the GPU reads and writes directly (over
+  // the CPU-GPU link) instead of device memory: relations kept out of HBM
+  bool host = false;
 
   void* get(size_t bytes) {
     bytes = bytes ? (bytes + 255) & ~size_t(255) : 256;
@@ -132,7 +135,9 @@ class Pool {
   std::unordered_map<char*, Block> used_;
 
   void release(char* p, size_t bytes) {
-    if (ff)
+    if (host)
+      cudaFreeHost(p);
+    else if (ff)
       ff(p, bytes, ctx);
     else
       cudaFree(p);
@@ -140,7 +145,12 @@ class Pool {
 
   void* acquire(size_t want) {
     void* p = nullptr;
-    if (af) {
+    if (host) {
+      if (cudaHostAlloc(&p, want, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+      }
+    } else if (af) {
       p = af(want, ctx);
     } else if (cudaMalloc(&p, want) != cudaSuccess) {
       cudaGetLastError();
@@ -285,6 +295,7 @@ struct Relation {
   uint32_t bound[kMaxK] = {0, 0, 0, 0};  // every value of column k is <= bound[k]
   uint64_t version[2] = {1, 1};
   uint64_t delta_version = 0;  // the Full version the last merge made: Full = previous Full + delta
+  bool host_full = false;      // Full kept in pinned host memory (option host_full)
   // batched runs: the rows of instances that reached their fixpoint leave
   // full for this buffer (instance i: ret_cnt[i] rows from ret_off[i])
   DCols retired;
@@ -363,6 +374,7 @@ struct cdl_engine {
   cdl_options opt{};
   cudaStream_t st = nullptr;
   Pool pool;
+  Pool hpool;  // pinned host memory for relations kept out of device memory (option host_full)
   Profiler prof;
   Ctx ctx;
   std::string err;
@@ -565,6 +577,7 @@ struct cdl_engine {
     rels.clear();
     ctl.reset();
     pool.release_all();
+    hpool.release_all();
     if (h_ctl) cudaFreeHost(h_ctl);
     if (h_est) cudaFreeHost(h_est);
     if (h_batch) cudaFreeHost(h_batch);
@@ -588,6 +601,20 @@ struct cdl_engine {
       b.bytes = bytes;
     }
     return b;
+  }
+  // k columns of cap rows in pinned host memory (the GPU accesses them in place)
+  bool alloc_cols_host(DCols& d, uint32_t k, uint64_t cap) {
+    d.clear();
+    const size_t stride = col_stride(cap);
+    d.buf.p = hpool.get(stride * k);
+    if (!d.buf.p) return false;
+    d.buf.pool = &hpool;
+    d.buf.bytes = stride * k;
+    d.k = k;
+    d.cap = cap;
+    for (uint32_t i = 0; i < k; ++i)
+      d.c[i] = reinterpret_cast<uint32_t*>(static_cast<char*>(d.buf.p) + stride * i);
+    return true;
   }
   bool alloc_cols(DCols& d, uint32_t k, uint64_t cap) {
     d.clear();
@@ -659,8 +686,9 @@ struct cdl_engine {
   cdl_status merge_into(Relation& r, DCols& fresh, DCols* delta_out, uint32_t delta_slot) {
     if (r.dsm.on) return dsm_diff(r, fresh, delta_out, delta_slot);
     DCols merged, delta;
-    if (!alloc_cols(merged, r.arity, r.full.n + fresh.n) || !alloc_cols(delta, r.arity, fresh.n))
-      return fail(CDL_E_NOMEM, "merge buffers");
+    const bool ok = r.host_full ? alloc_cols_host(merged, r.arity, r.full.n + fresh.n)
+                                : alloc_cols(merged, r.arity, r.full.n + fresh.n);
+    if (!ok || !alloc_cols(delta, r.arity, fresh.n)) return fail(CDL_E_NOMEM, "merge buffers");
     DBuf ws = alloc(diff_merge_workspace(r.full.n, fresh.n));
     if (!ws.p) return fail(CDL_E_NOMEM, "merge workspace");
     cudaError_t e = diff_merge(ctx, r.arity, r.full.in(), r.full.n, fresh.in(), fresh.n,
@@ -691,6 +719,8 @@ struct cdl_engine {
       Relation& R = *rels[i];
       R.dsm.reset();
       R.dsm.on = opt.dedup > 0 && R.idb && !full_read[i] && !opt.n_instances;
+      // out of core: Full that only step (d) reads lives in pinned host memory
+      R.host_full = opt.host_full > 0 && R.idb && !full_read[i] && !opt.n_instances && !R.dsm.on;
     }
   }
 
@@ -2107,7 +2137,7 @@ struct cdl_engine {
   // index, and every derived relation is the head of a recorded chain.
   bool graph_plan() {
     for (auto& r : rels)
-      if (r->dsm.on) return false;  // the captured round is the merge form
+      if (r->dsm.on || r->host_full) return false;  // the captured round keeps Full on the device
     if (grec_bad || grec.empty() || opt.estimator) return false;
     std::vector<bool> active(rels.size(), false);
     for (size_t ri = 0; ri < rules.size(); ++ri) {
@@ -2766,7 +2796,7 @@ struct cdl_engine {
       for (const DCols* d : {&R.full, &R.delta})
         for (uint32_t k = 0; k < R.arity && ok && d->n; ++k) {
           col.resize(d->n);
-          if (cudaMemcpy(col.data(), d->c[k], 4 * d->n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+          if (cudaMemcpy(col.data(), d->c[k], 4 * d->n, cudaMemcpyDefault) != cudaSuccess) {
             std::fclose(f);
             return fail(CDL_E_CUDA, "checkpoint copy");
           }
@@ -3197,6 +3227,7 @@ cdl_status cdl_relation_export(cdl_engine* e, cdl_rel rel, uint32_t* const* cols
   const cdl_status f = e->flush_loads();
   if (f != CDL_OK) return f;
   const Relation& R = *e->rels[rel];
+  (void)on_device;  // the copies infer both sides' memory (Full may be host-resident)
   *n_written = R.full.n;
   if (cap < R.full.n) return e->fail(CDL_E_CAPACITY, "export buffer too small");
   if (R.full.n == 0) return CDL_OK;
@@ -3204,8 +3235,8 @@ cdl_status cdl_relation_export(cdl_engine* e, cdl_rel rel, uint32_t* const* cols
   cudaError_t er = cudaSuccess;
   for (uint32_t k = 0; k < R.arity && er == cudaSuccess; ++k) {
     if (!cols[k]) return e->fail(CDL_E_INVALID, "null column pointer");
-    er = cudaMemcpyAsync(cols[k], R.full.c[k], R.full.n * 4,
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, e->st);
+    // Full may be in device or (option host_full) pinned host memory
+    er = cudaMemcpyAsync(cols[k], R.full.c[k], R.full.n * 4, cudaMemcpyDefault, e->st);
   }
   if (er == cudaSuccess) er = cudaStreamSynchronize(e->st);
   return er == cudaSuccess ? CDL_OK : e->cuda_fail(er, "export");
@@ -3226,6 +3257,7 @@ cdl_status cdl_relation_export_rows(cdl_engine* e, cdl_rel rel, uint64_t first, 
   const cdl_status f = e->flush_loads();
   if (f != CDL_OK) return f;
   const Relation& R = *e->rels[rel];
+  (void)on_device;  // the copies infer both sides' memory (Full may be host-resident)
   if (first > R.full.n || count > R.full.n - first)
     return e->fail(CDL_E_CAPACITY, "row range past the relation");
   if (count == 0) return CDL_OK;
@@ -3233,8 +3265,7 @@ cdl_status cdl_relation_export_rows(cdl_engine* e, cdl_rel rel, uint64_t first, 
   cudaError_t er = cudaSuccess;
   for (uint32_t k = 0; k < R.arity && er == cudaSuccess; ++k) {
     if (!cols[k]) return e->fail(CDL_E_INVALID, "null column pointer");
-    er = cudaMemcpyAsync(cols[k], R.full.c[k] + first, count * 4,
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, e->st);
+    er = cudaMemcpyAsync(cols[k], R.full.c[k] + first, count * 4, cudaMemcpyDefault, e->st);
   }
   if (er == cudaSuccess) er = cudaStreamSynchronize(e->st);
   return er == cudaSuccess ? CDL_OK : e->cuda_fail(er, "export rows");
