@@ -345,6 +345,8 @@ def bench_gb300(args, rank, world, dist):
         form.update(graph=True)
     if args.dedup:
         form.update(dedup=args.dedup)
+    if args.host_full:
+        form.update(host_full=1)
     trained = None
     if spec.get("learned"):
         params, nsamp, tsec = train_estimator(spec, rank)
@@ -557,6 +559,9 @@ def bench_gb300(args, rank, world, dist):
         config["autotune"] = "6 tuning runs (untimed), then the cached choices"
     if spec.get("graph"):
         config["graph"] = "rounds 3.. as one CUDA graph (conditional while node)"
+    if args.host_full:
+        config["host_full"] = ("Full of relations only step (d) reads in pinned host memory, "
+                               "merged in place over the CPU-GPU link")
     if args.dedup:
         config["dedup"] = ("Algorithm 2, hybrid index (decomposed Full: per-column sorted ids "
                            "+ unique hashmap)" if args.dedup == 1 else
@@ -599,6 +604,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sg-forest-200k", choices=sorted(WORKLOADS))
     ap.add_argument("--scale", type=float, default=None, help="points-to scale factor")
+    ap.add_argument("--host-full", action="store_true",
+                    help="keep Full of relations only step (d) reads in pinned host memory")
     ap.add_argument("--dedup", type=int, default=0, choices=[0, 1, 2],
                     help="step (d): 0 merge of sorted rows, 1 Algorithm 2 (hybrid index), "
                          "2 Algorithm 2 (hash-only index)")

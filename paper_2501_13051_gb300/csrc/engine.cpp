@@ -164,6 +164,10 @@ class Pool {
   bool grow(size_t bytes) {
     trim();
     size_t want = std::max(bytes, size_t(64) << 20);
+    // pinning host memory costs far more than a device allocation: host
+    // chunks grow geometrically, so a relation growing every round pins
+    // O(log) times
+    if (host) want = std::max(bytes * 2, size_t(1) << 30);
     if (limit && held + want > limit) {
       want = bytes;
       if (held + want > limit) return false;
