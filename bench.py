@@ -82,6 +82,7 @@ WORKLOADS = {
                        sample=dict(kind="owl", triples=1_000_000, seed=4),
                        train=dict(kind="owl", triples=2_000_000, seed=104)),
     "batched-512": dict(kind="batch", count=512, seed=5, lo=1e3, hi=5e5, learned=True, tune=True,
+                        graph_also=True,
                         desc="512 independent fixpoints in one batched run (instance column "
                              "leading): TC on even, SG on odd instances, directed ER graphs "
                              "with log-uniform 1e3..5e5 edges, mean out-degree 0.9; launch "
@@ -458,6 +459,33 @@ def bench_gb300(args, rank, world, dist):
                    "form": "learned join-size estimator (count pass skipped where predicted, "
                            "build side by cost), exact fallback"}
 
+    # ---- rounds in one captured graph (the tuner's choices, no estimator:
+    # a predicted join's check is a host decision), retirement on the device
+    graph_line = None
+    if spec.get("graph_also"):
+        gform = {k: v for k, v in form.items() if k not in ("estimator", "est_params")}
+        gform["graph"] = True
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        gd, grounds, gret = 0, 0, 0
+        for i in range(args.steps):
+            if i:
+                flush.fill_(i & 0xFF)
+            gst = step(False, extra=gform)[0]
+            gd += gst.derived_tuples
+            grounds += gst.graph_rounds
+            gret += gst.graph_retirements
+        g1.record()
+        torch.cuda.synchronize()
+        gsecs = g0.elapsed_time(g1) * 1e-3
+        graph_line = {"tuples_per_s": gd / gsecs, "ms_per_step": 1e3 * gsecs / args.steps,
+                      "graph_rounds_per_step": grounds / args.steps,
+                      "device_retirements_per_step": gret / args.steps,
+                      "form": "rounds after the first semi-naive one in one captured CUDA graph "
+                              "(conditional while node), converged instances retired on the "
+                              "device, autotuned launch parameters"}
+
     # ---- the round's new tuples as sorted rows (radix sort + unique) instead
     # of bitmaps, where the bitmap form is the default: timed the same way
     rows = None
@@ -566,6 +594,8 @@ def bench_gb300(args, rank, world, dist):
         config["dedup"] = ("Algorithm 2, hybrid index (decomposed Full: per-column sorted ids "
                            "+ unique hashmap)" if args.dedup == 1 else
                            "Algorithm 2, hash-only index (multimap of column 0)")
+    if graph_line is not None:
+        config["graph_form"] = graph_line
     if learned is not None:
         config["learned_form"] = learned
     if rows is not None:

@@ -192,4 +192,14 @@ __device__ __forceinline__ uint64_t dev_size(const uint64_t* dn, uint64_t cap) {
   return v < cap ? v : cap;
 }
 
+// Grid of a launch over `tiles` tiles.  A device-sized launch (dn set: a
+// captured round, its tiles counted for a capacity) gets at most kDevGrid
+// blocks, which loop over the tiles the actual size gives, so that rounds
+// far below the capacity do not launch blocks by the hundred thousand;
+// other launches get one block per tile (one iteration of the loop).
+constexpr uint64_t kDevGrid = 152 * 8;
+inline unsigned dev_grid(uint64_t tiles, const void* dn) {
+  return (unsigned)(dn && tiles > kDevGrid ? kDevGrid : (tiles ? tiles : 1));
+}
+
 }  // namespace cdl

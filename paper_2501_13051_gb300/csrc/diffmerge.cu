@@ -275,17 +275,16 @@ __global__ void __launch_bounds__(kDT, 5) k_merge_write(ColsIn F, uint64_t nF, C
                                                      const uint64_t* __restrict__ splits,
                                                      const uint32_t* __restrict__ corank,
                                                      const uint64_t* __restrict__ tile_pre,
-                                                     ColsOut D, ColsOut M, DevMerge dm) {
+                                                     ColsOut D, ColsOut M, DevMerge dm,
+                                                     uint64_t ntiles) {
   __shared__ uint32_t shift[kShiftWords];
   __shared__ uint32_t red[kDT / 32 + 1];
-  const uint64_t tile = blockIdx.x;
-  uint64_t ntiles = 0;
-  if (!resolve(dm, F, nF, nU, ntiles)) return;
+  if (!resolve(dm, F, nF, nU, ntiles)) return;  // (inside a captured round: sizes from the device)
   if (dm.n_full) {
-    if (tile >= ntiles) return;
     D = *dm.delta;
     M = *dm.merged;
   }
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
   const uint64_t d0 = tile * kDTile;
   const uint64_t d1 = d0 + kDTile < nF + nU ? d0 + kDTile : nF + nU;
   const uint64_t a0 = splits[tile], a1 = splits[tile + 1];
@@ -344,10 +343,9 @@ __global__ void __launch_bounds__(kDT, 5) k_merge_write(ColsIn F, uint64_t nF, C
     }
     __syncthreads();
   }
-  if (!merged) return;
   // the Full slice, four loads in flight per thread and column
   constexpr int kU = 8;
-  for (uint32_t base = 0; base < na; base += kU * kDT) {
+  for (uint32_t base = 0; merged && base < na; base += kU * kDT) {
     uint32_t v[kU][K];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
@@ -364,6 +362,8 @@ __global__ void __launch_bounds__(kDT, 5) k_merge_write(ColsIn F, uint64_t nF, C
         for (int k = 0; k < K; ++k) M.c[k][at] = v[u][k];
       }
     }
+  }
+  __syncthreads();  // the next tile rebuilds the shift table
   }
 }
 
@@ -435,8 +435,8 @@ cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, u
   // part of the writes (merged and delta) is added once its size is known
   const double mb = merged.c[0] ? 4.0 * K * n_full : 0.0;
   ProfScope p(c, kDiffMerge, 4.0 * K * (n_full + n_fresh) + mb);
-  k_merge_write<K><<<(unsigned)tiles, kDT, 0, c.st>>>(full, n_full, fresh, n_fresh, splits, corank,
-                                                      pre, delta, merged, dm);
+  k_merge_write<K><<<dev_grid(tiles, dm.n_full), kDT, 0, c.st>>>(
+      full, n_full, fresh, n_fresh, splits, corank, pre, delta, merged, dm, tiles);
   return cudaGetLastError();
 }
 

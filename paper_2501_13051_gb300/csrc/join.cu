@@ -71,23 +71,26 @@ __global__ void __launch_bounds__(kCT) k_join_count(const JoinSpec j, uint32_t* 
   __shared__ uint64_t red[kCT / 32 + 1];
   const uint64_t n = dev_size(j.dn, j.n_probe);
   const ColsIn probe = probe_cols(j);
-  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
-  if (base >= n && blockIdx.x > 0) return;
   const uint64_t mask = j.slots - 1;
-  uint64_t s = 0;
+  // tile 0 is written even for n == 0; blocks loop over the tiles
+  const uint64_t ntiles = n ? (n + kScanTile - 1) / kScanTile : 1;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t base = tile * kScanTile;
+    uint64_t s = 0;
 #pragma unroll 4
-  for (int i = 0; i < kCItems; ++i) {
-    const uint64_t row = base + (uint64_t)i * kCT + threadIdx.x;
-    if (row < n) {
-      uint32_t st;
-      const uint32_t cnt = lookup(j, probe, mask, row, &st);
-      counts[row] = cnt;
-      s += cnt;
+    for (int i = 0; i < kCItems; ++i) {
+      const uint64_t row = base + (uint64_t)i * kCT + threadIdx.x;
+      if (row < n) {
+        uint32_t st;
+        const uint32_t cnt = lookup(j, probe, mask, row, &st);
+        counts[row] = cnt;
+        s += cnt;
+      }
     }
+    uint64_t total;
+    block_exclusive_sum<kCT, uint64_t>(s, red, &total);  // ends with a barrier
+    if (threadIdx.x == 0) tile_sums[tile] = total;
   }
-  uint64_t total;
-  block_exclusive_sum<kCT, uint64_t>(s, red, &total);
-  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
 __global__ void __launch_bounds__(kCT) k_join_count_only(const JoinSpec j,
@@ -164,19 +167,22 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
   const uint64_t n_probe = dev_size(j.dn, j.n_probe);
   const ColsIn probe = probe_cols(j);
   total = dev_size(dtotal, total);
-  if (dbase) base = *dbase;
+  const uint64_t wbase = dbase ? *dbase : base;  // rows of this join start here
+  (void)wbase;  // (a bitmap head writes no rows)
   const uint64_t nm = n_probe + total;
-  const uint64_t d0 = (uint64_t)blockIdx.x * kJTile;
-  if (d0 >= nm) return;  // beyond a device-given size
+  const uint64_t ntiles = (nm + kJTile - 1) / kJTile;  // a device-given size may be below the grid's
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  {
+  const uint64_t d0 = tile * kJTile;
   const uint64_t d1 = d0 + kJTile < nm ? d0 + kJTile : nm;
   if (splits) {
-    if (threadIdx.x < 2) s_split[threadIdx.x] = splits[blockIdx.x + threadIdx.x];
+    if (threadIdx.x < 2) s_split[threadIdx.x] = splits[tile + threadIdx.x];
   } else {
     if (threadIdx.x == 0) s_split[0] = merge_split(off, n_probe, total, d0);
     if (threadIdx.x == 32) s_split[1] = merge_split(off, n_probe, total, d1);
   }
   // (a device-sized launch had its range claimed by the split kernel)
-  if (!FILTER && !DENSE && !dbase && blockIdx.x == 0 && threadIdx.x == 0)
+  if (!FILTER && !DENSE && !dbase && tile == 0 && threadIdx.x == 0)
     atomicAdd(cursor, (unsigned long long)total);
   __syncthreads();
   const uint64_t j0 = s_split[0], j1 = s_split[1];
@@ -223,7 +229,8 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
     }
     return tuple_of(r_lo + lo, (uint64_t)s_start[lo] + (o - s_off[lo]), vals);
   };
-  if (DENSE && nrows <= kDRows) {
+  if constexpr (DENSE) {
+   if (nrows <= kDRows) {
     // a few probe rows with long ranges (the hot keys): the block walks
     // each row's outputs in turn, with no search for the row
     bool bad = false;
@@ -244,9 +251,7 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
       }
     }
     if (bad && err) atomicOr(err, kErrCapacity);
-    return;
-  }
-  if (DENSE) {
+   } else {
     // kDU outputs per thread at a time, each stage's loads all in flight:
     // the gathers, the words' reads, the atomics of missing bits
     bool bad = false;
@@ -269,8 +274,9 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
         if (need[u]) atomicOr(dset.words + word[u], bit[u]);
     }
     if (bad && err) atomicOr(err, kErrCapacity);
-    return;
+   }
   }
+  if constexpr (!DENSE)
   for (uint64_t ob = o0; ob < o1; ob += kJT) {
     const uint64_t o = ob + threadIdx.x;
     const bool valid = o < o1;
@@ -285,7 +291,7 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
       pos = s_base + local;
       __syncthreads();
     } else {
-      pos = base + o;
+      pos = wbase + o;
     }
     if (keep) {
       if (pos < out_cap) {
@@ -296,6 +302,9 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
         if (err) atomicOr(err, kErrCapacity);
       }
     }
+  }
+  }
+  __syncthreads();  // the next tile restages the offsets and splits
   }
 }
 
@@ -322,7 +331,8 @@ cudaError_t join_count_scan(Ctx& c, const JoinSpec& j, uint64_t* d_off, uint64_t
   {
     const double keyb = j.pk1 == 0xFFu ? 4.0 : 8.0;
     ProfScope p(c, kJoinCount, (keyb + 16.0 + 4.0) * j.n_probe);
-    k_join_count<<<(unsigned)tiles, kCT, 0, c.st>>>(j, counts, static_cast<uint64_t*>(scan_ws));
+    k_join_count<<<dev_grid(tiles, j.dn), kCT, 0, c.st>>>(j, counts,
+                                                           static_cast<uint64_t*>(scan_ws));
   }
   return scan_finish(c, counts, j.n_probe, d_off, d_total, scan_ws, j.dn);
 }
@@ -562,16 +572,16 @@ cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_
   uint32_t* err = d_soft_err ? d_soft_err : c.d_err;
   const DenseSet ds = dense ? *dense : DenseSet{};
   if (dense && filter)
-    k_join_write<true, true><<<(unsigned)blocks, kJT, 0, c.st>>>(
+    k_join_write<true, true><<<dev_grid(blocks, d_total), kJT, 0, c.st>>>(
         j, d_off, total, out, base, cur, out_cap, splits, err, d_total, d_base, ds);
   else if (dense)
-    k_join_write<false, true><<<(unsigned)blocks, kJT, 0, c.st>>>(
+    k_join_write<false, true><<<dev_grid(blocks, d_total), kJT, 0, c.st>>>(
         j, d_off, total, out, base, cur, out_cap, splits, err, d_total, d_base, ds);
   else if (filter)
-    k_join_write<true, false><<<(unsigned)blocks, kJT, 0, c.st>>>(
+    k_join_write<true, false><<<dev_grid(blocks, d_total), kJT, 0, c.st>>>(
         j, d_off, total, out, base, cur, out_cap, splits, err, d_total, d_base, ds);
   else
-    k_join_write<false, false><<<(unsigned)blocks, kJT, 0, c.st>>>(
+    k_join_write<false, false><<<dev_grid(blocks, d_total), kJT, 0, c.st>>>(
         j, d_off, total, out, base, cur, out_cap, splits, err, d_total, d_base, ds);
   return cudaGetLastError();
 }

@@ -21,17 +21,20 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
                                                               const uint64_t* dn) {
   __shared__ uint64_t red[kScanThreads / 32 + 1];
   n = dev_size(dn, n);
-  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
-  if (base >= n && blockIdx.x > 0) return;  // beyond a device-given size
-  uint64_t s = 0;
+  // tile 0 is written even for n == 0; blocks loop over the tiles
+  const uint64_t ntiles = n ? (n + kScanTile - 1) / kScanTile : 1;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t base = tile * kScanTile;
+    uint64_t s = 0;
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const uint64_t idx = base + (uint64_t)i * kScanThreads + threadIdx.x;
-    if (idx < n) s += __ldg(in + idx);
+    for (int i = 0; i < kScanItems; ++i) {
+      const uint64_t idx = base + (uint64_t)i * kScanThreads + threadIdx.x;
+      if (idx < n) s += __ldg(in + idx);
+    }
+    uint64_t total;
+    block_exclusive_sum<kScanThreads, uint64_t>(s, red, &total);  // ends with a barrier
+    if (threadIdx.x == 0) tile_sums[tile] = total;
   }
-  uint64_t total;
-  block_exclusive_sum<kScanThreads, uint64_t>(s, red, &total);
-  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
 // One block: exclusive scan of the tile sums of n items in place; total ->
@@ -61,31 +64,32 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
   __shared__ uint32_t s_in[pad_idx(kScanTile) + 1];
   __shared__ uint64_t red[kScanThreads / 32 + 1];
   n = dev_size(dn, n);
-  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
-  if (base >= n) return;
-  // striped, coalesced load into shared memory
+  for (uint64_t tile = blockIdx.x; tile * kScanTile < n; tile += gridDim.x) {
+    const uint64_t base = tile * kScanTile;
+    // striped, coalesced load into shared memory
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const uint32_t l = i * kScanThreads + threadIdx.x;
-    const uint64_t idx = base + l;
-    s_in[pad_idx(l)] = idx < n ? __ldg(in + idx) : 0u;
-  }
-  __syncthreads();
-  // blocked: thread t owns tile elements [t*ITEMS, (t+1)*ITEMS)
-  uint32_t v[kScanItems];
-  uint64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+      const uint32_t l = i * kScanThreads + threadIdx.x;
+      const uint64_t idx = base + l;
+      s_in[pad_idx(l)] = idx < n ? __ldg(in + idx) : 0u;
+    }
+    __syncthreads();
+    // blocked: thread t owns tile elements [t*ITEMS, (t+1)*ITEMS)
+    uint32_t v[kScanItems];
+    uint64_t s = 0;
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    v[i] = s_in[pad_idx(threadIdx.x * kScanItems + i)];
-    s += v[i];
-  }
-  uint64_t tot;
-  uint64_t run = block_exclusive_sum<kScanThreads, uint64_t>(s, red, &tot) + prefix[blockIdx.x];
-  const uint64_t first = base + (uint64_t)threadIdx.x * kScanItems;
+    for (int i = 0; i < kScanItems; ++i) {
+      v[i] = s_in[pad_idx(threadIdx.x * kScanItems + i)];
+      s += v[i];
+    }
+    uint64_t tot;
+    uint64_t run = block_exclusive_sum<kScanThreads, uint64_t>(s, red, &tot) + prefix[tile];
+    const uint64_t first = base + (uint64_t)threadIdx.x * kScanItems;
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    if (first + i < n) out[first + i] = run;
-    run += v[i];
+    for (int i = 0; i < kScanItems; ++i) {
+      if (first + i < n) out[first + i] = run;
+      run += v[i];
+    }
   }
 }
 
@@ -140,7 +144,7 @@ cudaError_t exclusive_scan(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out
   uint64_t* sums = static_cast<uint64_t*>(ws);
   {
     ProfScope p(c, c.scan_cls, 4.0 * n);
-    k_scan_reduce<<<(unsigned)tiles, kScanThreads, 0, c.st>>>(in, n, sums, dn);
+    k_scan_reduce<<<dev_grid(tiles, dn), kScanThreads, 0, c.st>>>(in, n, sums, dn);
   }
   return scan_finish(c, in, n, out, d_total, ws, dn);
 }
@@ -159,7 +163,7 @@ cudaError_t scan_finish(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out, u
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
   uint64_t* sums = static_cast<uint64_t*>(ws);
   k_scan_top<<<1, kTopThreads, 0, c.st>>>(sums, n, d_total, dn);
-  k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, c.st>>>(in, n, sums, out, dn);
+  k_scan_apply<<<dev_grid(tiles, dn), kScanThreads, 0, c.st>>>(in, n, sums, out, dn);
   return cudaGetLastError();
 }
 

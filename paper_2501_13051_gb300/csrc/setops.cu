@@ -85,10 +85,11 @@ __global__ void k_mark_instances(const uint32_t* __restrict__ inst, uint64_t n,
     n = dev_size(dn, n);
     round += *dround;
   }
-  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t v = __ldg(inst + i);
-  if ((i == 0 || __ldg(inst + i - 1) != v) && v < n_instances) last_round[v] = round;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = __ldg(inst + i);
+    if ((i == 0 || __ldg(inst + i - 1) != v) && v < n_instances) last_round[v] = round;
+  }
 }
 
 // bounds[i] = the first row whose instance id (column 0, sorted) is >= i,
@@ -238,8 +239,8 @@ cudaError_t mark_instances(Ctx& c, const uint32_t* inst, uint64_t n, uint32_t n_
                            const uint64_t* dn, const uint64_t* dround) {
   if (n == 0) return cudaSuccess;
   ProfScope p(c, kMisc, 4.0 * n);
-  k_mark_instances<<<(unsigned)((n + 255) / 256), 256, 0, c.st>>>(inst, n, n_instances, last_round,
-                                                                  round, dinst, dn, dround);
+  k_mark_instances<<<dev_grid((n + 255) / 256, dinst), 256, 0, c.st>>>(
+      inst, n, n_instances, last_round, round, dinst, dn, dround);
   return cudaGetLastError();
 }
 

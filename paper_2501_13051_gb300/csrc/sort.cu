@@ -41,31 +41,33 @@ __global__ void __launch_bounds__(T) k_radix_upsweep(ColsIn in, uint64_t n, Pass
                                                      uint64_t* d_cells) {
   constexpr int R = 1 << BITS;
   constexpr int kRT = T, kRTile = T * kRItems;
-  if (dn) {  // device-given size: the grid covers the capacity
+  if (dn) {  // device-given size: the blocks loop over the tiles it gives
     n = dev_size(dn, n);
     ntiles = (n + kRTile - 1) / kRTile;
     // the length of the digit-major counts the pass's scan covers
     if (blockIdx.x == 0 && threadIdx.x == 0) *d_cells = (uint64_t)R * ntiles;
-    if (blockIdx.x >= ntiles) return;
   }
   __shared__ uint32_t h[R];
-  for (int i = threadIdx.x; i < R; i += kRT) h[i] = 0;
-  __syncthreads();
-  const uint64_t base = (uint64_t)blockIdx.x * kRTile;
-  uint32_t v[kRItems][K];
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int i = threadIdx.x; i < R; i += kRT) h[i] = 0;
+    __syncthreads();
+    const uint64_t base = tile * kRTile;
+    uint32_t v[kRItems][K];
 #pragma unroll
-  for (int it = 0; it < kRItems; ++it) {  // every load in flight before the first use
-    const uint64_t idx = base + (uint64_t)it * kRT + threadIdx.x;
+    for (int it = 0; it < kRItems; ++it) {  // every load in flight before the first use
+      const uint64_t idx = base + (uint64_t)it * kRT + threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[it][k] = (idx < n && p.mask[k]) ? __ldg(in.c[k] + idx) : 0u;
+      for (int k = 0; k < K; ++k) v[it][k] = (idx < n && p.mask[k]) ? __ldg(in.c[k] + idx) : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kRItems; ++it) {
+      const uint64_t idx = base + (uint64_t)it * kRT + threadIdx.x;
+      if (idx < n) atomicAdd(&h[digit_of<K>(v[it], p)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < R; i += kRT) tile_hist[(uint64_t)i * ntiles + tile] = h[i];
+    __syncthreads();
   }
-#pragma unroll
-  for (int it = 0; it < kRItems; ++it) {
-    const uint64_t idx = base + (uint64_t)it * kRT + threadIdx.x;
-    if (idx < n) atomicAdd(&h[digit_of<K>(v[it], p)], 1u);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < R; i += kRT) tile_hist[(uint64_t)i * ntiles + blockIdx.x] = h[i];
 }
 
 // Three resident blocks of 512 threads (or six of 256) per SM: registers
@@ -77,10 +79,9 @@ __global__ void __launch_bounds__(T, 1536 / T) k_radix_scatter(ColsIn in, ColsOu
                                                              uint64_t ntiles, const uint64_t* dn) {
   constexpr int R = 1 << BITS;
   constexpr int kRT = T, kRTile = T * kRItems, kRW = T / 32;
-  if (dn) {  // device-given size: the grid covers the capacity
+  if (dn) {  // device-given size: the blocks loop over the tiles it gives
     n = dev_size(dn, n);
     ntiles = (n + kRTile - 1) / kRTile;
-    if (blockIdx.x >= ntiles) return;
   }
   constexpr int DPT = (R + kRT - 1) / kRT;
   __shared__ uint32_t wh[kRW][R];  // per-warp digit counts, then per-warp offsets
@@ -90,10 +91,11 @@ __global__ void __launch_bounds__(T, 1536 / T) k_radix_scatter(ColsIn in, ColsOu
                                    // gstart[d] + i)
   __shared__ uint32_t red[kRT / 32 + 1];
   extern __shared__ uint32_t stage[];  // K x kRTile
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
   for (int i = threadIdx.x; i < kRW * R; i += kRT) (&wh[0][0])[i] = 0;
   __syncthreads();
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-  const uint64_t base = (uint64_t)blockIdx.x * kRTile;
+  const uint64_t base = tile * kRTile;
   const uint64_t wbase = base + (uint64_t)warp * 32 * kRItems;
   uint32_t v[kRItems][K];
   uint32_t rk[kRItems];
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(T, 1536 / T) k_radix_scatter(ColsIn in, ColsOu
       s += t;
     }
     tstart[d] = s;
-    gstart[d] = off ? off[(uint64_t)d * ntiles + blockIdx.x] : 0ull;
+    gstart[d] = off ? off[(uint64_t)d * ntiles + tile] : 0ull;
   }
   __syncthreads();
   {  // tile-local digit starts: exclusive scan of the digit totals
@@ -173,6 +175,8 @@ __global__ void __launch_bounds__(T, 1536 / T) k_radix_scatter(ColsIn in, ColsOu
     const uint64_t g = gstart[d] + i;
 #pragma unroll
     for (int k = 0; k < K; ++k) out.c[k][g] = t[k];
+  }
+  __syncthreads();  // the next tile reuses the shared tables and the staging buffer
   }
 }
 
@@ -226,15 +230,15 @@ cudaError_t sort_passes(Ctx& c, const RadixPlan& plan, ColsOut a, ColsOut b, uin
     if (!single) {
       {
         ProfScope ps(c, kRadixUpsweep, 4.0 * cols_used * n + 4.0 * cells);
-        k_radix_upsweep<K, BITS, T><<<(unsigned)ntiles, kRT, 0, c.st>>>(in, n, p, hist, ntiles, dn,
-                                                                        d_cells);
+        k_radix_upsweep<K, BITS, T><<<dev_grid(ntiles, dn), kRT, 0, c.st>>>(in, n, p, hist, ntiles,
+                                                                            dn, d_cells);
       }
       e = exclusive_scan(c, hist, cells, off, nullptr, scan_ws, d_cells);
       if (e != cudaSuccess) return e;
     }
     {
       ProfScope ps(c, kRadixScatter, 8.0 * K * n);
-      k_radix_scatter<K, BITS, T><<<(unsigned)ntiles, kRT, smem, c.st>>>(
+      k_radix_scatter<K, BITS, T><<<dev_grid(ntiles, dn), kRT, smem, c.st>>>(
           in, dst, n, p, single ? nullptr : off, ntiles, dn);
     }
     e = cudaGetLastError();
