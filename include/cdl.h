@@ -157,6 +157,15 @@ typedef struct {
                            checkpoints read it where it is.  Not with dedup or batched
                            runs; no graph rounds.  0 = default, Full in device memory.
                            Results never depend on it */
+  int32_t star;         /* a rule whose join chain ends with two atoms that both key only on
+                           variables of the probe side before them (same generation's
+                           edge(a, x), sg(a, b), edge(b, y)): 0 = default, one join probes
+                           both atoms' hash indexes from each probe row and writes the head
+                           tuples for every pair of matched rows (count pass: the product
+                           of the two range lengths), so the table of the first join's
+                           results is never written; -1 = a chain of binary joins
+                           (Algorithm 1) throughout.  A probe row with 2^32 or more
+                           outputs raises CDL_E_CAPACITY.  Results never depend on it */
 } cdl_options;
 
 /* Fills *opts with the defaults (everything zero / NULL except the
@@ -243,6 +252,7 @@ typedef struct {
   uint64_t graph_retirements; /* batched runs with options.graph: rounds of the captured
                              graph in which converged instances' rows left Full (decided and
                              moved on the device) */
+  uint64_t star_joins;    /* joins that probed two atoms from each probe row (options.star) */
 } cdl_stats;
 
 /* Runs the semi-naive loop to the fixpoint on the engine's stream and waits

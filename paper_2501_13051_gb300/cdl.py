@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
                 ("est_min_rows", ctypes.c_uint64), ("graph", ctypes.c_int32),
                 ("dense_bits", ctypes.c_int32), ("dedup", ctypes.c_int32),
                 ("plan_launch_bytes", ctypes.c_double), ("est_max_rows", ctypes.c_uint64),
-                ("host_full", ctypes.c_int32)]
+                ("host_full", ctypes.c_int32), ("star", ctypes.c_int32)]
 
 MLP_IN = 16
 MLP_PARAMS = 5313
@@ -77,7 +77,8 @@ class Stats(ctypes.Structure):
                 ("delta_cap", ctypes.c_uint64),
                 ("iters_per_instance", ctypes.POINTER(ctypes.c_uint64)),
                 ("graph_rounds", ctypes.c_uint64), ("graph_builds", ctypes.c_uint64),
-                ("index_merges", ctypes.c_uint64), ("graph_retirements", ctypes.c_uint64)]
+                ("index_merges", ctypes.c_uint64), ("graph_retirements", ctypes.c_uint64),
+                ("star_joins", ctypes.c_uint64)]
 
 
 class ColRef(ctypes.Structure):
@@ -212,6 +213,7 @@ class RunStats:
     graph_builds: int = 0
     index_merges: int = 0
     graph_retirements: int = 0
+    star_joins: int = 0
 
 
 # kernel classes in cdl_kernel_profile order
@@ -242,7 +244,7 @@ class Engine:
                  timing=False, hash_load=0.5, radix_bits=0, torch_alloc=True, estimator=0,
                  est_margin=1.0, est_params=None, n_instances=0, retire=True, autotune=0,
                  tune_cache=None, graph=False, est_min_rows=0, dense_bits=0, dedup=0,
-                 plan_launch_bytes=0.0, est_max_rows=0, host_full=0):
+                 plan_launch_bytes=0.0, est_max_rows=0, host_full=0, star=0):
         torch = _torch()
         L = lib()
         self._L = L
@@ -273,6 +275,7 @@ class Engine:
         opts.plan_launch_bytes = plan_launch_bytes
         opts.est_max_rows = est_max_rows
         opts.host_full = host_full  # 1: Full of step-(d)-only relations in pinned host memory
+        opts.star = star  # 0: chains ending in two probe-keyed atoms join them at once; -1 never
         opts.tune_cache = os.fsencode(tune_cache) if tune_cache else None
         self.n_instances = n_instances
         self._opts = opts
@@ -404,7 +407,7 @@ class Engine:
                         st.est_predictions, st.est_overflows,
                         [int(inst[i]) for i in range(self.n_instances)],
                         st.graph_rounds, st.graph_builds, st.index_merges,
-                        st.graph_retirements)
+                        st.graph_retirements, st.star_joins)
 
     # ---------------------------------------------------------- estimator
     def estimator_log(self):

@@ -394,6 +394,7 @@ struct cdl_engine {
   // with the round's delta (incremental maintenance) instead of a new sort
   std::vector<std::unique_ptr<Index>> prev_full;
   uint64_t index_merges = 0;
+  uint64_t star_joins = 0;  // joins that probed two build sides from one probe row
   uint32_t radix_bits = 0;  // digit width 8, 9 or 10; 0: 8, or 9 where that saves a pass
   uint32_t digits_for(uint32_t total_bits) const {
     return radix_bits ? radix_bits : fit_digit_bits(total_bits, 8);
@@ -1292,6 +1293,28 @@ struct cdl_engine {
     return idx + 60.0 * (double)P.n;
   }
 
+  // Key columns of atom C probed from P beside a join of P with B (a star
+  // join): every variable C shares with P or B is one of P's, one or two of
+  // them (ckey: C's columns, cpkey: P's), and B shares a variable with P.
+  static bool star_keys(const Src& P, const Src& B, const Src& C, std::vector<uint32_t>& ckey,
+                        std::vector<uint32_t>& cpkey) {
+    ckey.clear();
+    cpkey.clear();
+    bool shared = false;
+    for (uint32_t v : B.vars) shared |= std::find(P.vars.begin(), P.vars.end(), v) != P.vars.end();
+    if (!shared) return false;
+    for (uint32_t cc = 0; cc < C.vars.size(); ++cc) {
+      auto it = std::find(P.vars.begin(), P.vars.end(), C.vars[cc]);
+      if (it != P.vars.end()) {
+        ckey.push_back(cc);
+        cpkey.push_back((uint32_t)(it - P.vars.begin()));
+      } else if (std::find(B.vars.begin(), B.vars.end(), C.vars[cc]) != B.vars.end()) {
+        return false;
+      }
+    }
+    return !ckey.empty() && ckey.size() <= 2;
+  }
+
   cdl_status eval_join(const RuleR& rule, const std::vector<int>& vers, size_t start) {
     const size_t nb_all = rule.body.size();
     std::vector<Src> atoms(nb_all);
@@ -1339,19 +1362,30 @@ struct cdl_engine {
     Src left = std::move(atoms[start]);
     for (size_t t = 1; t < nb; ++t) {
       Src& right = atoms[order[t]];
-      const bool last = t + 1 == nb;
+      bool last = t + 1 == nb;
+      // the chain's last atom, where it may join this step as a star
+      Src* const after = !last && t + 2 == nb && opt.star >= 0 && !est_plan
+                             ? &atoms[order[t + 1]] : nullptr;
+      std::vector<uint32_t> ckey, cpkey;
       // roles: the first join may build on either atom; later joins build on the atom
       bool build_right = true;
       if (t == 1) {
         const bool right_static = right.rel >= 0 && !rels[right.rel]->idb;
         const bool left_static = left.rel >= 0 && !rels[left.rel]->idb;
         if (!right_static && (left_static || left.n < right.n)) build_right = false;
-        // the learned form: the orientation that moves fewer bytes
-        if (opt.estimator >= 1 && !recording && !left.vars.empty() && !right.vars.empty())
+        // the learned form: the orientation that moves fewer bytes (a star
+        // join, which writes no intermediate table, is kept where it applies)
+        if (opt.estimator >= 1 && !recording && !left.vars.empty() && !right.vars.empty() &&
+            !(build_right && after && star_keys(left, right, *after, ckey, cpkey)))
           build_right = orient_bytes(right, left) <= orient_bytes(left, right);
       }
       Src& P = build_right ? left : right;
       Src& B = build_right ? right : left;
+      // a star join: the last atom keys on the probe side's variables alone,
+      // so both build sides are probed from each probe row and the table
+      // between the two joins is never written
+      Src* const C = after && build_right && star_keys(P, B, *after, ckey, cpkey) ? after : nullptr;
+      if (C) last = true;
       std::vector<uint32_t> pkey, bkey;
       for (uint32_t bc = 0; bc < B.vars.size(); ++bc) {
         auto it = std::find(P.vars.begin(), P.vars.end(), B.vars[bc]);
@@ -1364,11 +1398,14 @@ struct cdl_engine {
         auto it = std::find(P.vars.begin(), P.vars.end(), v);
         if (it != P.vars.end()) return Ref{0, (uint32_t)(it - P.vars.begin())};
         it = std::find(B.vars.begin(), B.vars.end(), v);
-        return Ref{1, (uint32_t)(it - B.vars.begin())};
+        if (it != B.vars.end() || !C) return Ref{1, (uint32_t)(it - B.vars.begin())};
+        it = std::find(C->vars.begin(), C->vars.end(), v);
+        return Ref{3, (uint32_t)(it - C->vars.begin())};
       };
       auto avail = [&](uint32_t v) {
         return std::find(P.vars.begin(), P.vars.end(), v) != P.vars.end() ||
-               std::find(B.vars.begin(), B.vars.end(), v) != B.vars.end();
+               std::find(B.vars.begin(), B.vars.end(), v) != B.vars.end() ||
+               (C && std::find(C->vars.begin(), C->vars.end(), v) != C->vars.end());
       };
       std::vector<uint32_t> hkey(bkey.begin(), bkey.begin() + std::min<size_t>(2, bkey.size()));
       JoinSpec js{};
@@ -1393,6 +1430,19 @@ struct cdl_engine {
         for (uint32_t c = 0; c < B.k; ++c) js.build.c[c] = ix->cols[c];
         js.table = static_cast<const Slot*>(ix->table.p);
         js.slots = ix->slots;
+      }
+      std::unique_ptr<Index> temp_ix2;
+      Index* ix2 = nullptr;
+      if (C) {
+        r = get_index(*C, ckey, &ix2, temp_ix2);
+        if (r != CDL_OK) return r;
+        js.star = 1;
+        js.qk0 = cpkey[0];
+        js.qk1 = cpkey.size() > 1 ? cpkey[1] : 0xFFu;
+        for (uint32_t c = 0; c < C->k; ++c) js.build2.c[c] = ix2->cols[c];
+        js.table2 = static_cast<const Slot*>(ix2->table.p);
+        js.slots2 = ix2->slots;
+        ++star_joins;
       }
       for (size_t q = 2; q < bkey.size(); ++q) {
         if (js.n_eq >= 4) return fail(CDL_E_INVALID, "too many shared variables");
@@ -1442,10 +1492,10 @@ struct cdl_engine {
       const std::tuple<size_t, size_t, size_t> step_key{(size_t)(&rule - rules.data()), start, t};
       // a prediction pays off where the count pass it saves is not trivial
       // (a dense head needs no buffer sized: its tuples become bits)
-      const bool predict = ix != nullptr && est_ready() && !force_exact &&
+      const bool predict = ix != nullptr && !js.star && est_ready() && !force_exact &&
                            !(last && rels[rule.head.rel]->dset.words) &&
                            P.n >= (opt.est_min_rows ? opt.est_min_rows : kPredictMinRows);
-      const bool feats = ix != nullptr && (predict || opt.estimator >= 2);
+      const bool feats = ix != nullptr && !js.star && (predict || opt.estimator >= 2);
       auto features = [&]() {
         const Relation* PR = P.rel >= 0 ? rels[P.rel].get() : nullptr;
         const auto po = prev_out.find(step_key);
@@ -1591,7 +1641,8 @@ struct cdl_engine {
       if (!off.p || !ws.p) return fail(CDL_E_NOMEM, "join offsets");
       // the probe cost per row measures the index's load factor for the tuner
       Tuner::Probe tp;
-      if (ix && !ix->tkey.empty() && tuner.mode == 2 && P.n >= 4096) {
+      // (a star join's count measures it where one index serves both sides)
+      if (ix && (!js.star || ix2 == ix) && !ix->tkey.empty() && tuner.mode == 2 && P.n >= 4096) {
         auto& ts = tuner.table[ix->tkey];
         if ((size_t)ix->tcand < ts.size() && ts[ix->tcand].n < Tuner::kTrials)
           tp = tuner.start(ix->tkey, ix->tcand, (double)P.n, st);
@@ -1620,7 +1671,8 @@ struct cdl_engine {
         g.seen_total = total;
         const bool first_ok = t > 1 || (P.rel >= 0 && P.ver == kDelta && rels[P.rel]->idb);
         const bool later_ok = t == 1 || P.rel < 0;
-        if (!ix || &P != &left || B.rel < 0 || rels[B.rel]->idb || !first_ok || !later_ok)
+        if (!ix || &P != &left || B.rel < 0 || rels[B.rel]->idb || !first_ok || !later_ok ||
+            (C && (C->rel < 0 || rels[C->rel]->idb)))
           grec_bad = true;
         grec.push_back(g);
       }
@@ -2158,7 +2210,9 @@ struct cdl_engine {
       std::vector<const GStep*> chain;
       for (const GStep& g : grec)
         if (g.rule == ri) chain.push_back(&g);
-      if (chain.size() + 1 != var_atoms) return false;
+      size_t covered = 1;  // atoms the recorded steps join (a star step joins two)
+      for (const GStep* g : chain) covered += 1 + g->js.star;
+      if (covered != var_atoms) return false;
       for (size_t i = 0; i < chain.size(); ++i)
         if (chain[i]->t != i + 1 || chain[i]->last != (i + 1 == chain.size())) return false;
       active[rule.head.rel] = true;
@@ -2569,6 +2623,7 @@ struct cdl_engine {
     prof.reset();
     joins = 0;
     index_merges = 0;
+    star_joins = 0;
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
@@ -2761,6 +2816,7 @@ struct cdl_engine {
       stats->graph_rounds = g_rounds;
       stats->graph_builds = g_builds;
       stats->index_merges = index_merges;
+      stats->star_joins = star_joins;
       stats->graph_retirements = g_retirements;
       if (stats->delta_per_round)
         for (uint64_t i = 0; i < per_round.size() && i < stats->delta_cap; ++i)

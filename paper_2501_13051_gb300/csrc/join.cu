@@ -59,6 +59,29 @@ __device__ __forceinline__ uint32_t lookup(const JoinSpec& j, const ColsIn& prob
                      start);
 }
 
+// Range of second-build-side rows matching probe row `row` (star joins).
+__device__ __forceinline__ uint32_t lookup2(const JoinSpec& j, const ColsIn& probe, uint64_t row,
+                                           uint32_t* start) {
+  const uint32_t k1 = j.qk1 == 0xFFu ? 0u : __ldg(col_of(probe, j.qk1) + row);
+  return probe_table(j.table2, j.slots2 - 1, __ldg(col_of(probe, j.qk0) + row), k1, start);
+}
+
+// Output count of probe row `row`: its range length, or for a star join the
+// product of its two range lengths (a product past 2^32 - 1 raises
+// kErrCapacity and counts 0: no relation holds that many rows).
+__device__ __forceinline__ uint32_t row_count(const JoinSpec& j, const ColsIn& probe,
+                                             uint64_t mask, uint64_t row, uint32_t* err) {
+  uint32_t st;
+  const uint32_t c1 = lookup(j, probe, mask, row, &st);
+  if (!j.star || c1 == 0) return c1;
+  const uint64_t prod = (uint64_t)c1 * lookup2(j, probe, row, &st);
+  if (prod > 0xFFFFFFFFull) {
+    if (err) atomicOr(err, kErrCapacity);
+    return 0;
+  }
+  return (uint32_t)prod;
+}
+
 // The probe side of a launch: the spec's columns and row count, or (inside
 // a captured round) the ones device memory holds, the count clamped to the
 // capacity the spec's n_probe then gives.
@@ -67,7 +90,8 @@ __device__ __forceinline__ ColsIn probe_cols(const JoinSpec& j) {
 }
 
 __global__ void __launch_bounds__(kCT) k_join_count(const JoinSpec j, uint32_t* __restrict__ counts,
-                                                    uint64_t* __restrict__ tile_sums) {
+                                                    uint64_t* __restrict__ tile_sums,
+                                                    uint32_t* err) {
   __shared__ uint64_t red[kCT / 32 + 1];
   const uint64_t n = dev_size(j.dn, j.n_probe);
   const ColsIn probe = probe_cols(j);
@@ -81,8 +105,7 @@ __global__ void __launch_bounds__(kCT) k_join_count(const JoinSpec j, uint32_t* 
     for (int i = 0; i < kCItems; ++i) {
       const uint64_t row = base + (uint64_t)i * kCT + threadIdx.x;
       if (row < n) {
-        uint32_t st;
-        const uint32_t cnt = lookup(j, probe, mask, row, &st);
+        const uint32_t cnt = row_count(j, probe, mask, row, err);
         counts[row] = cnt;
         s += cnt;
       }
@@ -94,11 +117,11 @@ __global__ void __launch_bounds__(kCT) k_join_count(const JoinSpec j, uint32_t* 
 }
 
 __global__ void __launch_bounds__(kCT) k_join_count_only(const JoinSpec j,
-                                                         uint32_t* __restrict__ counts) {
+                                                         uint32_t* __restrict__ counts,
+                                                         uint32_t* err) {
   const uint64_t row = (uint64_t)blockIdx.x * kCT + threadIdx.x;
   if (row >= j.n_probe) return;
-  uint32_t st;
-  counts[row] = lookup(j, j.probe, j.slots - 1, row, &st);
+  counts[row] = row_count(j, j.probe, j.slots - 1, row, err);
 }
 
 // Number of probe rows among the first d items of the merge of the row
@@ -145,14 +168,17 @@ __global__ void k_write_splits(const uint64_t* __restrict__ off, uint64_t n, uin
 }
 
 __device__ __forceinline__ uint32_t ref_value(const JoinSpec& j, const ColsIn& probe, const Ref& r,
-                                              uint64_t row, uint64_t brow) {
+                                              uint64_t row, uint64_t brow, uint64_t brow2 = 0) {
   if (r.side == 0) return __ldg(col_of(probe, r.v) + row);
   if (r.side == 1) return __ldg(j.build.c[r.v] + brow);
+  if (r.side == 3) return __ldg(j.build2.c[r.v] + brow2);
   return r.v;
 }
 
 // DENSE: each output tuple sets its bit in dset instead of being written.
-template <bool FILTER, bool DENSE>
+// STAR: output n of probe row j (local index l = n - pos_buf[j]) pairs the
+// first range's row l / c2 with the second range's row l % c2.
+template <bool FILTER, bool DENSE, bool STAR>
 __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint64_t* __restrict__ off,
                                                     uint64_t total, ColsOut out, uint64_t base,
                                                     unsigned long long* cursor, uint64_t out_cap,
@@ -161,11 +187,18 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
                                                     const uint64_t* dbase, const DenseSet dset) {
   __shared__ uint64_t s_off[kJTile + 1];
   __shared__ uint32_t s_start[kJTile + 1];
+  __shared__ uint32_t s_start2[STAR ? kJTile + 1 : 1];  // second range: start, length
+  __shared__ uint32_t s_cnt2[STAR ? kJTile + 1 : 1];
   __shared__ uint64_t s_split[2];
   __shared__ uint32_t red[kJT / 32 + 1];
   __shared__ unsigned long long s_base;
   const uint64_t n_probe = dev_size(j.dn, j.n_probe);
   const ColsIn probe = probe_cols(j);
+  // a device-given join size past the capacity the launch was sized for:
+  // the outputs past it are not written, so the round must be redone (a
+  // filtered join's survivors may still have fit: the flag is conservative)
+  if (dtotal && blockIdx.x == 0 && threadIdx.x == 0 && *dtotal > total && err)
+    atomicOr(err, kErrCapacity);
   total = dev_size(dtotal, total);
   const uint64_t wbase = dbase ? *dbase : base;  // rows of this join start here
   (void)wbase;  // (a bitmap head writes no rows)
@@ -198,24 +231,42 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
     if (b > a) lookup(j, probe, mask, row, &st);
     s_off[r] = a;
     s_start[r] = st;
+    if constexpr (STAR) {
+      uint32_t st2 = 0, c2 = 1;
+      if (b > a) c2 = lookup2(j, probe, row, &st2);
+      s_start2[r] = st2;
+      s_cnt2[r] = c2;
+    }
   }
   __syncthreads();
   // head values of probe row `row` matched with build row `brow`; false
   // when a filter drops the pair
-  auto tuple_of = [&](uint64_t row, uint64_t brow, uint32_t (&vals)[kMaxK]) -> bool {
+  auto tuple_of = [&](uint64_t row, uint64_t brow, uint64_t brow2,
+                      uint32_t (&vals)[kMaxK]) -> bool {
 #pragma unroll
     for (int k = 0; k < kMaxK; ++k)
-      if (k < (int)j.out_k) vals[k] = ref_value(j, probe, j.out[k], row, brow);
+      if (k < (int)j.out_k) vals[k] = ref_value(j, probe, j.out[k], row, brow, brow2);
     bool keep = true;
     if (FILTER) {
       for (uint32_t q = 0; q < j.n_eq; ++q)
-        keep &= ref_value(j, probe, j.eq[q][0], row, brow) ==
-                ref_value(j, probe, j.eq[q][1], row, brow);
+        keep &= ref_value(j, probe, j.eq[q][0], row, brow, brow2) ==
+                ref_value(j, probe, j.eq[q][1], row, brow, brow2);
       for (uint32_t q = 0; q < j.n_neq; ++q)
-        keep &= ref_value(j, probe, j.neq[q][0], row, brow) !=
-                ref_value(j, probe, j.neq[q][1], row, brow);
+        keep &= ref_value(j, probe, j.neq[q][0], row, brow, brow2) !=
+                ref_value(j, probe, j.neq[q][1], row, brow, brow2);
     }
     return keep;
+  };
+  // output l of staged row r (l < its range length, or the product of both)
+  auto tuple_in = [&](uint32_t r, uint64_t l, uint32_t (&vals)[kMaxK]) -> bool {
+    if constexpr (STAR) {
+      const uint32_t c2 = s_cnt2[r];
+      const uint32_t l1 = (uint32_t)l / c2;
+      return tuple_of(r_lo + r, (uint64_t)s_start[r] + l1,
+                      (uint64_t)s_start2[r] + ((uint32_t)l - l1 * c2), vals);
+    } else {
+      return tuple_of(r_lo + r, (uint64_t)s_start[r] + l, 0, vals);
+    }
   };
   // output o of the block: its probe row found in the staged offsets
   auto tuple_at = [&](uint64_t o, uint32_t (&vals)[kMaxK]) -> bool {
@@ -227,7 +278,7 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
       else
         hi = mid;
     }
-    return tuple_of(r_lo + lo, (uint64_t)s_start[lo] + (o - s_off[lo]), vals);
+    return tuple_in(lo, o - s_off[lo], vals);
   };
   if constexpr (DENSE) {
    if (nrows <= kDRows) {
@@ -241,7 +292,7 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
       const uint64_t b = e < o1 ? e : o1;
       for (uint64_t o = a + threadIdx.x; o < b; o += kJT) {
         uint32_t vals[kMaxK] = {0, 0, 0, 0};
-        if (!tuple_of(r_lo + r, (uint64_t)s_start[r] + (o - ra), vals)) continue;
+        if (!tuple_in(r, o - ra, vals)) continue;
         uint32_t word, bit;
         if (!dense_locate(dset, vals, &word, &bit)) {
           bad = true;
@@ -313,7 +364,8 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
 cudaError_t join_count_only(Ctx& c, const JoinSpec& j, uint32_t* counts) {
   if (j.n_probe == 0) return cudaSuccess;
   ProfScope p(c, kJoinCount, (j.pk1 == 0xFFu ? 4.0 : 8.0) * j.n_probe + 20.0 * j.n_probe);
-  k_join_count_only<<<(unsigned)((j.n_probe + kCT - 1) / kCT), kCT, 0, c.st>>>(j, counts);
+  k_join_count_only<<<(unsigned)((j.n_probe + kCT - 1) / kCT), kCT, 0, c.st>>>(j, counts,
+                                                                              c.d_err);
   return cudaGetLastError();
 }
 
@@ -329,10 +381,13 @@ cudaError_t join_count_scan(Ctx& c, const JoinSpec& j, uint64_t* d_off, uint64_t
   void* scan_ws = static_cast<char*>(ws) + (((j.n_probe * sizeof(uint32_t)) + 255) & ~size_t(255));
   const uint64_t tiles = (j.n_probe + kScanTile - 1) / kScanTile;
   {
-    const double keyb = j.pk1 == 0xFFu ? 4.0 : 8.0;
+    // per row: its key, the slot probed, the count written (a star join's
+    // second key and slot are read for rows its first range matches)
+    double keyb = j.pk1 == 0xFFu ? 4.0 : 8.0;
+    if (j.star) keyb += (j.qk1 == 0xFFu ? 4.0 : 8.0) + 16.0;
     ProfScope p(c, kJoinCount, (keyb + 16.0 + 4.0) * j.n_probe);
     k_join_count<<<dev_grid(tiles, j.dn), kCT, 0, c.st>>>(j, counts,
-                                                           static_cast<uint64_t*>(scan_ws));
+                                                           static_cast<uint64_t*>(scan_ws), c.d_err);
   }
   return scan_finish(c, counts, j.n_probe, d_off, d_total, scan_ws, j.dn);
 }
@@ -517,6 +572,7 @@ __global__ void __launch_bounds__(kDirT) k_join_heavy(const JoinSpec j, ColsOut 
 cudaError_t join_direct(Ctx& c, const JoinSpec& j, ColsOut out, uint64_t* d_cursor,
                         uint64_t out_cap, uint64_t* d_total, uint32_t* d_overflow,
                         const HeavyList& heavy) {
+  if (j.star) return cudaErrorInvalidValue;  // star joins keep the count pass
   if (j.n_probe == 0) return cudaSuccess;
   uint64_t blocks = (j.n_probe + kDirT - 1) / kDirT;
   if (blocks > 152 * 8) blocks = 152 * 8;
@@ -557,32 +613,38 @@ cudaError_t join_write(Ctx& c, const JoinSpec& j, const uint64_t* d_off, uint64_
         reinterpret_cast<unsigned long long*>(d_cursor), d_base, out_cap,
         d_soft_err ? d_soft_err : c.d_err);
   }
-  // per probe row: two offsets, key, re-probed slot, its own head columns;
-  // per output: the gathered build columns and the written head columns
+  // per probe row: two offsets, key, re-probed slot (a star join: both
+  // keys and slots), its own head columns; per output: the gathered build
+  // columns and the written head columns
   uint32_t nbuild = 0, nprobe = 0;
   for (uint32_t k = 0; k < j.out_k; ++k) {
-    nbuild += j.out[k].side == 1;
+    nbuild += j.out[k].side == 1 || j.out[k].side == 3;
     nprobe += j.out[k].side == 0;
   }
+  const double row_b = j.star ? 16.0 + 8.0 + 32.0 : 16.0 + 4.0 + 16.0;
   // (a dense head's bits are set in L2-resident words, not written out)
-  const double bytes = (16.0 + 4.0 + 16.0 + 4.0 * nprobe) * j.n_probe +
+  const double bytes = (row_b + 4.0 * nprobe) * j.n_probe +
                        (4.0 * nbuild + (dense ? 0.0 : 4.0 * j.out_k)) * total;
   ProfScope p(c, kJoinWrite, bytes);
   auto* cur = reinterpret_cast<unsigned long long*>(d_cursor);
   uint32_t* err = d_soft_err ? d_soft_err : c.d_err;
   const DenseSet ds = dense ? *dense : DenseSet{};
-  if (dense && filter)
-    k_join_write<true, true><<<dev_grid(blocks, d_total), kJT, 0, c.st>>>(
-        j, d_off, total, out, base, cur, out_cap, splits, err, d_total, d_base, ds);
-  else if (dense)
-    k_join_write<false, true><<<dev_grid(blocks, d_total), kJT, 0, c.st>>>(
-        j, d_off, total, out, base, cur, out_cap, splits, err, d_total, d_base, ds);
-  else if (filter)
-    k_join_write<true, false><<<dev_grid(blocks, d_total), kJT, 0, c.st>>>(
-        j, d_off, total, out, base, cur, out_cap, splits, err, d_total, d_base, ds);
-  else
-    k_join_write<false, false><<<dev_grid(blocks, d_total), kJT, 0, c.st>>>(
-        j, d_off, total, out, base, cur, out_cap, splits, err, d_total, d_base, ds);
+  const unsigned grid = dev_grid(blocks, d_total);
+#define CDL_JOIN_WRITE(F, D, S)                                                          \
+  k_join_write<F, D, S><<<grid, kJT, 0, c.st>>>(j, d_off, total, out, base, cur, out_cap, \
+                                                splits, err, d_total, d_base, ds)
+  if (j.star) {
+    if (dense && filter) CDL_JOIN_WRITE(true, true, true);
+    else if (dense) CDL_JOIN_WRITE(false, true, true);
+    else if (filter) CDL_JOIN_WRITE(true, false, true);
+    else CDL_JOIN_WRITE(false, false, true);
+  } else {
+    if (dense && filter) CDL_JOIN_WRITE(true, true, false);
+    else if (dense) CDL_JOIN_WRITE(false, true, false);
+    else if (filter) CDL_JOIN_WRITE(true, false, false);
+    else CDL_JOIN_WRITE(false, false, false);
+  }
+#undef CDL_JOIN_WRITE
   return cudaGetLastError();
 }
 

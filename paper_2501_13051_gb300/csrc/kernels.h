@@ -102,7 +102,7 @@ cudaError_t scan_finish(Ctx& c, const uint32_t* in, uint64_t n, uint64_t* out, u
 
 // -------------------------------------------------------------------- join
 struct Ref {
-  uint8_t side;  // 0 probe, 1 build, 2 constant
+  uint8_t side;  // 0 probe, 1 build, 2 constant, 3 second build side (star joins)
   uint32_t v;
 };
 struct JoinSpec {
@@ -124,6 +124,15 @@ struct JoinSpec {
   // memory (n_probe is then the capacity that sizes the grids); else null
   const ColsIn* dprobe;
   const uint64_t* dn;
+  // star join: a second build side, also keyed on probe columns (qk0, qk1;
+  // qk1 = 0xFF for one word).  A probe row then matches every pair of a row
+  // of its first range and a row of its second (count c1 * c2), the join of
+  // the chain's last two atoms with no intermediate table between them.
+  uint32_t star;
+  uint32_t qk0, qk1;
+  ColsIn build2;
+  const Slot* table2;
+  uint64_t slots2;
 };
 size_t join_count_workspace(uint64_t n_probe);
 // Pass 1 alone: counts[i] for every probe row.

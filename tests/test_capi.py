@@ -46,7 +46,7 @@ def test_structs_match_header_sizes():
     assert ctypes.sizeof(cdl.Term) == 8
     assert ctypes.sizeof(cdl.ColRef) == 8
     assert ctypes.sizeof(cdl.Atom) == 16
-    assert ctypes.sizeof(cdl.Stats) == 8 * 16
+    assert ctypes.sizeof(cdl.Stats) == 8 * 17
 
 
 def test_struct_sizes_equal_the_c_compilers(tmp_path):

@@ -19,13 +19,14 @@ def cdl():
     return C
 
 
-@pytest.mark.parametrize("count,seed,lo,hi,retire", [(12, 77, 50, 3000, True),
-                                                    (12, 77, 50, 3000, False),
-                                                    (33, 78, 20, 800, True)])
-def test_batched_equals_each_instance(cdl, oracle_lib, count, seed, lo, hi, retire):
+@pytest.mark.parametrize("count,seed,lo,hi,retire,star", [(12, 77, 50, 3000, True, 0),
+                                                         (12, 77, 50, 3000, False, 0),
+                                                         (33, 78, 20, 800, True, 0),
+                                                         (33, 78, 20, 800, True, -1)])
+def test_batched_equals_each_instance(cdl, oracle_lib, count, seed, lo, hi, retire, star):
     graphs, kinds = W.batched_instances(count, seed, lo, hi)
     prog = W.batched_program(graphs, kinds)
-    with cdl.Engine(n_instances=count, retire=retire, timing=True) as e:
+    with cdl.Engine(n_instances=count, retire=retire, timing=True, star=star) as e:
         e.load_program(prog)
         st = e.run()
         rel = {"tc": e.export("tc_path"), "sg": e.export("sg")}
@@ -44,6 +45,8 @@ def test_batched_equals_each_instance(cdl, oracle_lib, count, seed, lo, hi, reti
         assert np.array_equal(mine, want.relations["path" if k == "tc" else "sg"]), i
         assert st.iters_per_instance[i] == want.iterations, i
     assert max(st.iters_per_instance) == st.iterations
+    # sg's recursive rule keys both edge atoms on (instance, delta sg's columns)
+    assert (st.star_joins > 0) == (star == 0)
 
 
 def test_export_of_one_instance(cdl):

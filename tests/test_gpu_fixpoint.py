@@ -104,6 +104,60 @@ def test_random_programs(cdl, oracle_lib, seed, dense):
     check(cdl, oracle_lib, W.random_program(seed), dense_bits=dense)
 
 
+STAR_FORMS = pytest.mark.parametrize("star", [0, -1], ids=["star", "chain"])
+
+
+@STAR_FORMS
+@pytest.mark.parametrize("dense", [0, -1], ids=["dense", "sorted"])
+@pytest.mark.parametrize("make", [W.sg_program, W.sg_paper_program])
+def test_same_generation_star_and_chain(cdl, oracle_lib, make, dense, star):
+    """The recursive rule edge(a, x), sg(a, b), edge(b, y): with star joins
+    delta sg probes edge's index on a and on b and writes (x, y) for every
+    pair of matches; as a chain of binary joins it writes (x, b) first."""
+    st = check(cdl, oracle_lib, make(W.random_forest(3000, 7)), dense_bits=dense, star=star)
+    assert (st.star_joins > 0) == (star == 0)
+
+
+@STAR_FORMS
+def test_points_to_star_and_chain(cdl, oracle_lib, star):
+    # memoryAlias(x, w) :- dereference(y, x), valueAlias(y, z), dereference(z, w)
+    st = check(cdl, oracle_lib, W.points_to_program(W.points_to_edb(1 / 2048, 5)), dense_bits=-1,
+               star=star)
+    assert (st.star_joins > 0) == (star == 0)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_programs_as_chains(cdl, oracle_lib, seed):
+    check(cdl, oracle_lib, W.random_program(seed), dense_bits=-1, star=-1)
+
+
+def test_random_programs_take_star_joins(cdl):
+    # the same programs with star joins on (their parity: test_random_programs)
+    n = sum(cdl.run_program(W.random_program(s), dense_bits=-1)[1].star_joins for s in range(40))
+    assert n > 0
+
+
+@pytest.mark.parametrize("star", [0, -1], ids=["star", "chain"])
+def test_star_join_row_past_2_32_outputs(cdl, star):
+    """One probe row of q(x, y) :- e(a, x), s(a, b), e(b, y) meets 2^16
+    edges on each side: 2^32 outputs, one more than a relation holds.  The
+    star join's count pass flags the product, the chain's second join its
+    total; both stop with CDL_E_CAPACITY."""
+    kids = np.arange(1 << 16, dtype=np.uint32)
+    e = np.concatenate([np.stack([np.full(1 << 16, 1, np.uint32), 100 + kids], axis=1),
+                        np.stack([np.full(1 << 16, 2, np.uint32), 70000 + kids], axis=1)])
+    R = W.Rule
+    prog = W.Program({"e": 2, "s0": 2, "s": 2, "q": 2},
+                     [R(("s", ("a", "b")), (("s0", ("a", "b")),)),
+                      R(("q", ("x", "y")), (("e", ("a", "x")), ("s", ("a", "b")), ("e", ("b", "y"))))],
+                     {"e": e, "s0": np.array([[1, 2]], dtype=np.uint32)})
+    with cdl.Engine(dense_bits=-1, star=star) as eng:
+        eng.load_program(prog)
+        with pytest.raises(cdl.CdlError) as err:
+            eng.run()
+    assert cdl.STATUS[err.value.status] == "CDL_E_CAPACITY"
+
+
 @pytest.mark.parametrize("opts", [dict(radix_bits=8), dict(radix_bits=9), dict(radix_bits=10), dict(hash_load=0.8), dict(timing=True)])
 def test_engine_options_do_not_change_results(cdl, oracle_lib, opts):
     check(cdl, oracle_lib, W.sg_program(W.random_forest(1500, 5)), **opts)

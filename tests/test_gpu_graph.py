@@ -43,8 +43,14 @@ def test_transitive_closure_as_graph(cdl, oracle_lib, n, m, seed, graph):
                                   lambda: W.sg_paper_program(W.random_forest(3000, 32)),
                                   lambda: W.sg_program(W.random_forest(5000, 33))])
 def test_same_generation_as_graph(cdl, oracle_lib, make, graph):
-    # two joins per round (edge, delta sg, edge), with and without x != y
+    # one star join per round (delta sg probing edge twice), with and without x != y
     check(cdl, oracle_lib, make(), graph=graph)
+
+
+@pytest.mark.parametrize("graph", [True, 64])
+def test_same_generation_as_graph_with_binary_joins(cdl, oracle_lib, graph):
+    # two captured joins per round (edge, delta sg, edge) and the table between them
+    check(cdl, oracle_lib, W.sg_program(W.random_forest(3000, 34)), graph=graph, star=-1)
 
 
 def test_graph_runs_the_rounds_on_the_device(cdl, oracle_lib):
