@@ -11,13 +11,14 @@
 // (Green, McColl & Bader, "GPU merge path", ICS 2012), computed for all
 // tiles at once by a small kernel with one thread per split.  Then:
 //   count  -- per tile, every New tuple finds its co-rank in the tile's Full
-//             slice (how many of its Full tuples are <= it) by binary
-//             search, which also tells whether it repeats a Full tuple; a
-//             tile with many New tuples first stages its Full slice in
-//             shared memory, a sparse one searches with cached global loads
-//             and touches few Full sectors.  The co-rank of every New tuple
-//             (or a repeat mark) and the tile's count of new tuples are
-//             stored;
+//             slice (how many of its Full tuples are <= it) and whether it
+//             repeats a Full tuple.  A tile with many New tuples stages both
+//             slices in shared memory and merges them again, each thread
+//             walking 16 items from its own merge-path split; a sparse one
+//             binary-searches its Full slice with cached global loads, two
+//             searches per thread stepping together, and touches few Full
+//             sectors.  The co-rank of every New tuple (or a repeat mark)
+//             and the tile's count of new tuples are stored;
 //   scan   -- exclusive scan of the tile counts: each tile's delta offset
 //             and |delta|;
 //   write  -- per tile, a block scan ranks its new tuples, a histogram of
@@ -93,95 +94,83 @@ __global__ void k_merge_splits(ColsIn F, uint64_t nF, ColsIn U, uint64_t nU,
   splits[t] = merge_split<K>(F, nF, U, nU, d);
 }
 
-template <int K>
-__device__ __forceinline__ bool eq_at(const ColsIn& a, uint64_t i, const uint32_t (&t)[K]) {
-  bool e = true;
+// Co-ranks (or kRepeat) of the New tuples j + 32 q, q < Q (those below b1),
+// against the Full slice F[a0, a1) in global memory: the Q binary searches
+// step together, so each step issues Q independent loads per column and
+// their latencies overlap.  Every column of the probed Full tuple is read
+// at once, and equality is noted on the way: the search for the count of
+// tuples <= v tests the last one, so v is in the slice exactly when some
+// tested tuple equals it.  The tuple before the slice (same for the whole
+// tile) and the New tuple before j + 32 q are read up front.
+template <int K, int Q>
+__device__ __forceinline__ void co_ranks_global(const ColsIn& F, const ColsIn& U, uint64_t a0,
+                                                uint64_t a1, uint64_t j, uint64_t b1,
+                                                uint32_t (&p)[Q]) {
+  uint32_t v[Q][K];
+  bool rep[Q];
+  uint32_t lo[Q], hi[Q];
+  const uint32_t na = (uint32_t)(a1 - a0);
 #pragma unroll
-  for (int k = 0; k < K; ++k) e &= __ldg(a.c[k] + i) == t[k];
-  return e;
-}
-
-// Number of tuples <= t among s[0..n) (column k of item i at s[k*kDTile + i]).
-template <int K>
-__device__ __forceinline__ uint32_t count_le_smem(const uint32_t* s, uint32_t n,
-                                                  const uint32_t (&t)[K]) {
-  uint32_t lo = 0, hi = n;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    bool le = true;
+  for (int q = 0; q < Q; ++q) {
+    const uint64_t jq = j + 32u * q;
+    const bool live = jq < b1;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const uint32_t x = s[k * kDTile + mid];
-      if (x != t[k]) {
-        le = x < t[k];
-        break;
-      }
-    }
-    if (le)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  return lo;
-}
-
-// Number of tuples <= t among F[lo..hi), as an index into F.
-template <int K>
-__device__ __forceinline__ uint64_t count_le_global(const ColsIn& F, uint64_t lo, uint64_t hi,
-                                                    const uint32_t (&t)[K]) {
-  while (lo < hi) {
-    const uint64_t mid = lo + ((hi - lo) >> 1);
-    bool le = true;
+    for (int k = 0; k < K; ++k) v[q][k] = live ? __ldg(U.c[k] + jq) : 0u;
+    bool r = live && jq > 0, f = live && a0 > 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const uint32_t x = __ldg(F.c[k] + mid);
-      if (x != t[k]) {
-        le = x < t[k];
-        break;
+      if (live && jq > 0) r &= __ldg(U.c[k] + jq - 1) == v[q][k];
+      if (live && a0 > 0) f &= __ldg(F.c[k] + a0 - 1) == v[q][k];
+    }
+    rep[q] = r || f;  // a repeat of the New tuple before it, or of the Full tuple before the slice
+    lo[q] = 0;
+    hi[q] = live ? na : 0u;
+  }
+  for (;;) {
+    bool any = false;
+    uint32_t x[Q][K];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const uint32_t mid = (lo[q] + hi[q]) >> 1;
+#pragma unroll
+      for (int k = 0; k < K; ++k) x[q][k] = lo[q] < hi[q] ? __ldg(F.c[k] + a0 + mid) : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      if (lo[q] >= hi[q]) continue;
+      any = true;
+      const uint32_t mid = (lo[q] + hi[q]) >> 1;
+      bool le = true, eq = true;
+#pragma unroll
+      for (int k = K - 1; k >= 0; --k) {  // lexicographic, column 0 most significant
+        if (x[q][k] != v[q][k]) {
+          le = x[q][k] < v[q][k];
+          eq = false;
+        }
+      }
+      if (le) {
+        lo[q] = mid + 1;
+        rep[q] |= eq;
+      } else {
+        hi[q] = mid;
       }
     }
-    if (le)
-      lo = mid + 1;
-    else
-      hi = mid;
+    if (!any) break;
   }
-  return lo;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) p[q] = rep[q] ? kRepeat : lo[q];
 }
 
-// Co-rank and repeat test of New tuple j (row of U) against the Full slice
-// F[a0, a1), staged in shared memory (s) for dense tiles; returns the
-// co-rank or kRepeat.
-template <int K, bool DENSE>
-__device__ __forceinline__ uint32_t co_rank(const ColsIn& F, const ColsIn& U, const uint32_t* s,
-                                            uint64_t a0, uint64_t a1, uint64_t j) {
-  uint32_t v[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = __ldg(U.c[k] + j);
-  if (j > 0 && eq_at<K>(U, j - 1, v)) return kRepeat;
-  // the Full tuple just before v in merged order is F[a0 + p - 1]
-  const uint32_t p = DENSE ? count_le_smem<K>(s, (uint32_t)(a1 - a0), v)
-                           : (uint32_t)(count_le_global<K>(F, a0, a1, v) - a0);
-  bool rep;
-  if (p > 0) {
-    if (DENSE) {
-      bool e = true;
-#pragma unroll
-      for (int k = 0; k < K; ++k) e &= s[k * kDTile + p - 1] == v[k];
-      rep = e;
-    } else {
-      rep = eq_at<K>(F, a0 + p - 1, v);
-    }
-  } else {
-    rep = a0 > 0 && eq_at<K>(F, a0 - 1, v);
-  }
-  return rep ? kRepeat : p;
-}
+// Shared-memory position of tile item i: one padding word per 32, so that
+// threads walking from splits about kDItems apart mostly hit distinct banks.
+__device__ __forceinline__ uint32_t spad(uint32_t i) { return i + (i >> 5); }
+constexpr int kSRow = kDTile + kDTile / 32;  // words per column of a staged tile
 
 // Persistent over groups of `group` tiles (1..8; grid = resident blocks).
 // Warp w takes tile w of the group: a tile without New tuples costs one
 // store, a sparse one (New < Full / 16) is searched by its warp alone with
 // cached global loads; dense tiles are then taken by the whole block, which
-// stages their Full slice in shared memory.  So a round whose few new tuples
+// stages their slices in shared memory and merges them.  So a round whose few new tuples
 // meet a large Full keeps every warp busy instead of one block per tile,
 // while a small merge (fewer tiles than eight per resident block) keeps one
 // tile per block.
@@ -191,7 +180,7 @@ __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t 
                                                    uint32_t* __restrict__ corank,
                                                    uint32_t* __restrict__ tile_cnt,
                                                    uint64_t ntiles, DevMerge dm, uint32_t group) {
-  extern __shared__ uint32_t s[];  // K x kDTile: the Full slice of a dense tile
+  extern __shared__ uint32_t s[];  // K x kSRow: the Full and New slices of a dense tile
   if (!resolve(dm, F, nF, nU, ntiles)) return;
   __shared__ uint32_t red[kDT / 32 + 1];
   constexpr int kW = kDT / 32;
@@ -209,11 +198,18 @@ __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t 
       const uint64_t b0 = d0 - a0, b1 = d1 - a1;
       const uint64_t na = a1 - a0, nb = b1 - b0;
       if (nb * 16 < na || nb == 0) {
+        // searches stepped together per lane: two for pairs, one for wider tuples
+        constexpr int kQ = K <= 2 ? 2 : 1;
         uint32_t cnt = 0;
-        for (uint64_t j = b0 + lane; j < b1; j += 32) {
-          const uint32_t p = co_rank<K, false>(F, U, s, a0, a1, j);
-          corank[j] = p;
-          cnt += p == kRepeat ? 0u : 1u;
+        for (uint64_t j = b0 + lane; j < b1; j += 32 * kQ) {
+          uint32_t p[kQ];
+          co_ranks_global<K, kQ>(F, U, a0, a1, j, b1, p);
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            if (j + 32u * q >= b1) break;
+            corank[j + 32u * q] = p[q];
+            cnt += p[q] == kRepeat ? 0u : 1u;
+          }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -230,32 +226,88 @@ __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t 
       const uint64_t d1 = d0 + kDTile < nF + nU ? d0 + kDTile : nF + nU;
       const uint64_t a0 = splits[t], a1 = splits[t + 1];
       const uint64_t b0 = d0 - a0, b1 = d1 - a1;
-      const uint32_t na = (uint32_t)(a1 - a0);
-      // stage the Full slice, eight loads per column in flight
+      const uint32_t na = (uint32_t)(a1 - a0), nb = (uint32_t)(b1 - b0), nm = na + nb;
+      // stage both slices, eight loads per column in flight: Full at
+      // items [0, na), New at [na, nm) of each column's row of s
       constexpr int kS = 8;
-      for (uint32_t base = 0; base < na; base += kS * kDT) {
+      for (uint32_t base = 0; base < nm; base += kS * kDT) {
         uint32_t v[kS][K];
 #pragma unroll
         for (int u = 0; u < kS; ++u) {
           const uint32_t i = base + u * kDT + threadIdx.x;
 #pragma unroll
-          for (int k = 0; k < K; ++k) v[u][k] = i < na ? __ldg(F.c[k] + a0 + i) : 0u;
+          for (int k = 0; k < K; ++k)
+            v[u][k] = i < na ? __ldg(F.c[k] + a0 + i) : i < nm ? __ldg(U.c[k] + b0 + (i - na)) : 0u;
         }
 #pragma unroll
         for (int u = 0; u < kS; ++u) {
           const uint32_t i = base + u * kDT + threadIdx.x;
-          if (i < na) {
+          if (i < nm) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) s[k * kDTile + i] = v[u][k];
+            for (int k = 0; k < K; ++k) s[k * kSRow + spad(i)] = v[u][k];
           }
         }
       }
       __syncthreads();
+      // each thread merges kDItems items of the tile from its merge-path
+      // split (Full before an equal New tuple): a New tuple's co-rank is the
+      // number of Full tuples passed, and it repeats the last Full tuple
+      // passed or the New tuple before it
       uint32_t cnt = 0;
-      for (uint64_t j = b0 + threadIdx.x; j < b1; j += kDT) {
-        const uint32_t p = co_rank<K, true>(F, U, s, a0, a1, j);
-        corank[j] = p;
-        cnt += p == kRepeat ? 0u : 1u;
+      const uint32_t m0 = threadIdx.x * kDItems < nm ? threadIdx.x * kDItems : nm;
+      const uint32_t m1 = m0 + kDItems < nm ? m0 + kDItems : nm;
+      if (m0 < m1) {
+        auto at = [&](uint32_t i, int k) { return s[k * kSRow + spad(i)]; };
+        auto le_items = [&](uint32_t x, uint32_t y) {  // item x <= item y (s positions)
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const uint32_t a = at(x, k), b = at(y, k);
+            if (a != b) return a < b;
+          }
+          return true;
+        };
+        uint32_t lo = m0 > nb ? m0 - nb : 0, hi = m0 < na ? m0 : na;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (le_items(mid, na + (m0 - mid - 1)))
+            lo = mid + 1;
+          else
+            hi = mid;
+        }
+        uint32_t i = lo, jn = m0 - lo;  // Full and New tuples before the thread's items
+        uint32_t lf[K], ln[K];           // last Full and last New tuple passed
+        bool hf = i > 0 || a0 > 0, hn = jn > 0 || b0 > 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          lf[k] = i > 0 ? at(i - 1, k) : a0 > 0 ? __ldg(F.c[k] + a0 - 1) : 0u;
+          ln[k] = jn > 0 ? at(na + jn - 1, k) : b0 > 0 ? __ldg(U.c[k] + b0 - 1) : 0u;
+        }
+        for (uint32_t m = m0; m < m1; ++m) {
+          bool take_full = jn >= nb;
+          if (!take_full && i < na) take_full = le_items(i, na + jn);
+          if (take_full) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) lf[k] = at(i, k);
+            hf = true;
+            ++i;
+          } else {
+            uint32_t v[K];
+            bool ef = hf, en = hn;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              v[k] = at(na + jn, k);
+              ef &= lf[k] == v[k];
+              en &= ln[k] == v[k];
+            }
+            const bool rep = ef || en;
+            corank[b0 + jn] = rep ? kRepeat : i;
+            cnt += rep ? 0u : 1u;
+#pragma unroll
+            for (int k = 0; k < K; ++k) ln[k] = v[k];
+            hn = true;
+            ++jn;
+          }
+        }
       }
       uint32_t tot;
       block_exclusive_sum<kDT, uint32_t>(cnt, red, &tot);
@@ -391,7 +443,7 @@ cudaError_t run_diff_merge(Ctx& c, ColsIn full, uint64_t n_full, ColsIn fresh, u
   void* scan_ws = w;
   uint64_t* d_tiles = nullptr;  // device-sized: the scan's length (the split kernel writes it)
   if (dm.n_full) d_tiles = reinterpret_cast<uint64_t*>(w + scan_workspace(tiles));
-  const size_t smem_count = sizeof(uint32_t) * K * kDTile;
+  const size_t smem_count = sizeof(uint32_t) * K * kSRow;
   // blocks of k_count_new<K> a whole GPU holds at once, per device
   constexpr int kDevices = 64;
   static int resident_of[kDevices] = {};
