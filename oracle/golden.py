@@ -42,7 +42,6 @@ def relation_digest(rows) -> str:
 # generator call; the test regenerates the same input from the same seed.
 SPECS = {
     "points-to-2e-9": dict(kind="pt", scale=1 / 512, seed=3),
-    "points-to-2e-6": dict(kind="pt", scale=1 / 64, seed=3),
     "owl-rl-20m": dict(kind="owl", triples=20_000_000, seed=4, entities=5_000_000),
     "sg-forest-50k": dict(kind="sg", n=50_000, seed=2),
     "batched-512": dict(kind="batch", count=512, seed=5, lo=1e3, hi=5e5),
