@@ -131,6 +131,28 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* smem, T* total) {
   return res;
 }
 
+// Exclusive max-scan over the block's threads (0 for thread 0).  smem:
+// THREADS/32 words.  Ends with a barrier.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_max(uint32_t v, uint32_t* smem) {
+  static_assert(THREADS % 32 == 0 && THREADS <= 1024, "whole warps");
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t n = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= (uint32_t)o) inc = n > inc ? n : inc;
+  }
+  const uint32_t ex_in_warp = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane == 31) smem[warp] = inc;
+  __syncthreads();
+  uint32_t before = 0;  // max over the earlier warps
+  for (uint32_t w = 0; w < warp; ++w) before = smem[w] > before ? smem[w] : before;
+  __syncthreads();
+  const uint32_t own = lane > 0 ? ex_in_warp : 0u;
+  return own > before ? own : before;
+}
+
 // A relation of arity k whose columns need T = bits_0 + ... + bits_{k-1}
 // bits in all can also be held as a bitmap of 2^T bits: tuple (v_0..v_{k-1})
 // is bit sum_k v_k << shift_k, with shift_k the bits of the columns after k.

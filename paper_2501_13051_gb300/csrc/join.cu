@@ -175,20 +175,30 @@ __device__ __forceinline__ uint32_t ref_value(const JoinSpec& j, const ColsIn& p
   return r.v;
 }
 
+// Row heads: five resident blocks per SM (registers capped at 51).  Bitmap
+// heads: registers capped at 32, eight blocks per SM (seven for star joins,
+// bounded by shared memory); the bit-setting loop is latency-bound, and on
+// points-to at 2^-5 this cap took the write from 6.6 s to 5.6 s per
+// fixpoint against four or five blocks.
 // DENSE: each output tuple sets its bit in dset instead of being written.
 // STAR: output n of probe row j (local index l = n - pos_buf[j]) pairs the
 // first range's row l / c2 with the second range's row l % c2.
 template <bool FILTER, bool DENSE, bool STAR>
-__global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint64_t* __restrict__ off,
+__global__ void __launch_bounds__(kJT, DENSE ? 8 : 5) k_join_write(const JoinSpec j, const uint64_t* __restrict__ off,
                                                     uint64_t total, ColsOut out, uint64_t base,
                                                     unsigned long long* cursor, uint64_t out_cap,
                                                     const uint64_t* __restrict__ splits,
                                                     uint32_t* err, const uint64_t* dtotal,
                                                     const uint64_t* dbase, const DenseSet dset) {
-  __shared__ uint64_t s_off[kJTile + 1];
+  // row r's first output: the carried-in row 0 keeps its global start,
+  // every later row starts inside the block's window of at most kJTile
+  // outputs and keeps its start relative to the window
+  __shared__ uint16_t s_loc[kJTile + 1];
+  __shared__ uint64_t s_a0;
   __shared__ uint32_t s_start[kJTile + 1];
   __shared__ uint32_t s_start2[STAR ? kJTile + 1 : 1];  // second range: start, length
   __shared__ uint32_t s_cnt2[STAR ? kJTile + 1 : 1];
+  __shared__ uint16_t s_row[DENSE ? 1 : kJTile];  // staged row of each of the block's outputs
   __shared__ uint64_t s_split[2];
   __shared__ uint32_t red[kJT / 32 + 1];
   __shared__ unsigned long long s_base;
@@ -223,14 +233,32 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
   const uint64_t r_lo = j0 > 0 ? j0 - 1 : 0;
   const uint32_t nrows = (uint32_t)(j1 - r_lo);
   const uint64_t mask = j.slots - 1;
+  // the outputs' rows come from a table where the head is written as rows
+  // (a bitmap head's block searches the staged starts, or walks its rows
+  // one by one when it has a few: there the table's barriers cost more
+  // than the searches they save)
+  constexpr bool table = !DENSE;
+  const uint32_t no = (uint32_t)(o1 - o0);
+  if constexpr (table) {
+    for (uint32_t i = threadIdx.x; i < no; i += kJT) s_row[i] = 0;
+    __syncthreads();
+  }
   for (uint32_t r = threadIdx.x; r < nrows; r += kJT) {
     const uint64_t row = r_lo + r;
     const uint64_t a = __ldg(off + row);
     const uint64_t b = row + 1 < n_probe ? __ldg(off + row + 1) : total;
     uint32_t st = 0;
     if (b > a) lookup(j, probe, mask, row, &st);
-    s_off[r] = a;
+    if (r == 0)
+      s_a0 = a;
+    else
+      s_loc[r] = (uint16_t)(a - o0);
     s_start[r] = st;
+    // a row with outputs in the block's window marks its first one there
+    // (such rows start at distinct outputs; the row carried in from the
+    // block before may end at the window's start)
+    const uint64_t first = a > o0 ? a : o0;
+    if (table && b > first && first < o1) s_row[first - o0] = (uint16_t)r;
     if constexpr (STAR) {
       uint32_t st2 = 0, c2 = 1;
       if (b > a) c2 = lookup2(j, probe, row, &st2);
@@ -239,6 +267,7 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
     }
   }
   __syncthreads();
+  auto off_of = [&](uint32_t r) -> uint64_t { return r == 0 ? s_a0 : o0 + s_loc[r]; };
   // head values of probe row `row` matched with build row `brow`; false
   // when a filter drops the pair
   auto tuple_of = [&](uint64_t row, uint64_t brow, uint64_t brow2,
@@ -268,17 +297,44 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
       return tuple_of(r_lo + r, (uint64_t)s_start[r] + l, 0, vals);
     }
   };
-  // output o of the block: its probe row found in the staged offsets
-  auto tuple_at = [&](uint64_t o, uint32_t (&vals)[kMaxK]) -> bool {
-    uint32_t lo = 0, hi = nrows;  // largest r with s_off[r] <= o
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (s_off[mid] <= o)
-        lo = mid;
-      else
-        hi = mid;
+  // every output takes the last mark at or before it: its row (the
+  // load-balanced search of Algorithm 1's write loop, a max-scan over the
+  // block's outputs instead of a binary search per output)
+  if constexpr (table) {
+    const uint32_t q0 = threadIdx.x * kJItems;
+    uint16_t loc[kJItems];
+    uint32_t m = 0;
+#pragma unroll
+    for (int q = 0; q < kJItems; ++q) {
+      loc[q] = q0 + q < no ? s_row[q0 + q] : (uint16_t)0;
+      m = loc[q] > m ? loc[q] : m;
     }
-    return tuple_in(lo, o - s_off[lo], vals);
+    uint32_t run = block_exclusive_max<kJT>(m, red);
+#pragma unroll
+    for (int q = 0; q < kJItems; ++q) {
+      run = loc[q] > run ? loc[q] : run;
+      if (q0 + q < no) s_row[q0 + q] = (uint16_t)run;
+    }
+    __syncthreads();
+  }
+  // output o of the block: its probe row from the table, or the last staged
+  // row starting at or before it
+  auto tuple_at = [&](uint64_t o, uint32_t (&vals)[kMaxK]) -> bool {
+    uint32_t r;
+    if constexpr (table) {
+      r = s_row[o - o0];
+    } else {
+      uint32_t lo = 0, hi = nrows;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (o0 + s_loc[mid] <= o)
+          lo = mid;
+        else
+          hi = mid;
+      }
+      r = lo;
+    }
+    return tuple_in(r, o - off_of(r), vals);
   };
   if constexpr (DENSE) {
    if (nrows <= kDRows) {
@@ -286,9 +342,9 @@ __global__ void __launch_bounds__(kJT) k_join_write(const JoinSpec j, const uint
     // each row's outputs in turn, with no search for the row
     bool bad = false;
     for (uint32_t r = 0; r < nrows; ++r) {
-      const uint64_t ra = s_off[r];
+      const uint64_t ra = off_of(r);
       const uint64_t a = ra > o0 ? ra : o0;
-      const uint64_t e = r + 1 < nrows ? s_off[r + 1] : o1;
+      const uint64_t e = r + 1 < nrows ? off_of(r + 1) : o1;
       const uint64_t b = e < o1 ? e : o1;
       for (uint64_t o = a + threadIdx.x; o < b; o += kJT) {
         uint32_t vals[kMaxK] = {0, 0, 0, 0};
