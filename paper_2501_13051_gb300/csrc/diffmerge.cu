@@ -12,9 +12,12 @@
 // tiles at once by a small kernel with one thread per split.  Then:
 //   count  -- per tile, every New tuple finds its co-rank in the tile's Full
 //             slice (how many of its Full tuples are <= it) and whether it
-//             repeats a Full tuple.  A tile with many New tuples stages both
-//             slices in shared memory and merges them again, each thread
-//             walking 16 items from its own merge-path split; a sparse one
+//             repeats a Full tuple.  A tile whose New tuples are at least a
+//             quarter of its Full ones stages both slices in shared memory
+//             and merges them again, each thread walking 16 items from its
+//             own merge-path split; one with fewer (but at least a
+//             sixteenth) stages its Full slice and searches it per New
+//             tuple; a sparse one
 //             binary-searches its Full slice with cached global loads, two
 //             searches per thread stepping together, and touches few Full
 //             sectors.  The co-rank of every New tuple (or a repeat mark)
@@ -166,6 +169,49 @@ __device__ __forceinline__ void co_ranks_global(const ColsIn& F, const ColsIn& U
 __device__ __forceinline__ uint32_t spad(uint32_t i) { return i + (i >> 5); }
 constexpr int kSRow = kDTile + kDTile / 32;  // words per column of a staged tile
 
+// Co-rank (or kRepeat) of New tuple j against a dense tile's Full slice of
+// na tuples staged in shared memory: a binary search, then the last Full
+// tuple <= it (or the one before the slice) and the New tuple before it
+// tell whether it repeats.
+template <int K>
+__device__ __forceinline__ uint32_t co_rank_smem(const ColsIn& F, const ColsIn& U,
+                                                 const uint32_t* s, uint64_t a0, uint32_t na,
+                                                 uint64_t j) {
+  uint32_t v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = __ldg(U.c[k] + j);
+  bool rep = j > 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (j > 0) rep &= __ldg(U.c[k] + j - 1) == v[k];
+  uint32_t lo = 0, hi = na;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    bool le = true;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint32_t x = s[k * kSRow + spad(mid)];
+      if (x != v[k]) {
+        le = x < v[k];
+        break;
+      }
+    }
+    if (le)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  bool eq = lo > 0 || a0 > 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (lo > 0)
+      eq &= s[k * kSRow + spad(lo - 1)] == v[k];
+    else if (a0 > 0)
+      eq &= __ldg(F.c[k] + a0 - 1) == v[k];
+  }
+  return rep || eq ? kRepeat : lo;
+}
+
 // Persistent over groups of `group` tiles (1..8; grid = resident blocks).
 // Warp w takes tile w of the group: a tile without New tuples costs one
 // store, a sparse one (New < Full / 16) is searched by its warp alone with
@@ -227,10 +273,14 @@ __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t 
       const uint64_t a0 = splits[t], a1 = splits[t + 1];
       const uint64_t b0 = d0 - a0, b1 = d1 - a1;
       const uint32_t na = (uint32_t)(a1 - a0), nb = (uint32_t)(b1 - b0), nm = na + nb;
-      // stage both slices, eight loads per column in flight: Full at
-      // items [0, na), New at [na, nm) of each column's row of s
+      // New at least a quarter of Full: both slices merged again; fewer New
+      // tuples: each searches the staged Full slice
+      const bool walk = (uint64_t)nb * 4 >= na;
+      const uint32_t nst = walk ? nm : na;
+      // stage the slices, eight loads per column in flight: Full at items
+      // [0, na), New (walk only) at [na, nm) of each column's row of s
       constexpr int kS = 8;
-      for (uint32_t base = 0; base < nm; base += kS * kDT) {
+      for (uint32_t base = 0; base < nst; base += kS * kDT) {
         uint32_t v[kS][K];
 #pragma unroll
         for (int u = 0; u < kS; ++u) {
@@ -242,7 +292,7 @@ __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t 
 #pragma unroll
         for (int u = 0; u < kS; ++u) {
           const uint32_t i = base + u * kDT + threadIdx.x;
-          if (i < nm) {
+          if (i < nst) {
 #pragma unroll
             for (int k = 0; k < K; ++k) s[k * kSRow + spad(i)] = v[u][k];
           }
@@ -256,7 +306,13 @@ __global__ void __launch_bounds__(kDT) k_count_new(ColsIn F, ColsIn U, uint64_t 
       uint32_t cnt = 0;
       const uint32_t m0 = threadIdx.x * kDItems < nm ? threadIdx.x * kDItems : nm;
       const uint32_t m1 = m0 + kDItems < nm ? m0 + kDItems : nm;
-      if (m0 < m1) {
+      if (!walk) {
+        for (uint64_t j = b0 + threadIdx.x; j < b1; j += kDT) {
+          const uint32_t p = co_rank_smem<K>(F, U, s, a0, na, j);
+          corank[j] = p;
+          cnt += p == kRepeat ? 0u : 1u;
+        }
+      } else if (m0 < m1) {
         auto at = [&](uint32_t i, int k) { return s[k * kSRow + spad(i)]; };
         auto le_items = [&](uint32_t x, uint32_t y) {  // item x <= item y (s positions)
 #pragma unroll
