@@ -21,6 +21,7 @@ namespace {
 // T threads per block (512 or 256, the tuner's choice) and kRItems tuples
 // per thread: a tile holds T * kRItems tuples.
 constexpr int kRItems = 8;
+static_assert(kRItems % 4 == 0, "the upsweep reads items in chunks of four");
 
 struct PassP {
   uint32_t sh[kMaxK], mask[kMaxK], dsh[kMaxK];
@@ -48,21 +49,46 @@ __global__ void __launch_bounds__(T) k_radix_upsweep(ColsIn in, uint64_t n, Pass
     if (blockIdx.x == 0 && threadIdx.x == 0) *d_cells = (uint64_t)R * ntiles;
   }
   __shared__ uint32_t h[R];
+  // the counts need no order: with every column at a 16-byte boundary a
+  // thread reads its items as 16-byte chunks of four (kRItems / 4 per
+  // column, every load in flight before the first use)
+  bool vec = true;
+#pragma unroll
+  for (int k = 0; k < K; ++k) vec &= (reinterpret_cast<uintptr_t>(in.c[k]) & 15u) == 0;
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     for (int i = threadIdx.x; i < R; i += kRT) h[i] = 0;
     __syncthreads();
     const uint64_t base = tile * kRTile;
     uint32_t v[kRItems][K];
+    if (vec && base + kRTile <= n) {
+      constexpr int kC = kRItems / 4;
 #pragma unroll
-    for (int it = 0; it < kRItems; ++it) {  // every load in flight before the first use
-      const uint64_t idx = base + (uint64_t)it * kRT + threadIdx.x;
+      for (int c = 0; c < kC; ++c) {
+        const uint64_t e0 = base + 4u * ((uint64_t)c * kRT + threadIdx.x);
 #pragma unroll
-      for (int k = 0; k < K; ++k) v[it][k] = (idx < n && p.mask[k]) ? __ldg(in.c[k] + idx) : 0u;
-    }
+        for (int k = 0; k < K; ++k) {
+          uint4 w = make_uint4(0u, 0u, 0u, 0u);
+          if (p.mask[k]) w = __ldg(reinterpret_cast<const uint4*>(in.c[k] + e0));
+          v[4 * c][k] = w.x;
+          v[4 * c + 1][k] = w.y;
+          v[4 * c + 2][k] = w.z;
+          v[4 * c + 3][k] = w.w;
+        }
+      }
 #pragma unroll
-    for (int it = 0; it < kRItems; ++it) {
-      const uint64_t idx = base + (uint64_t)it * kRT + threadIdx.x;
-      if (idx < n) atomicAdd(&h[digit_of<K>(v[it], p)], 1u);
+      for (int it = 0; it < kRItems; ++it) atomicAdd(&h[digit_of<K>(v[it], p)], 1u);
+    } else {
+#pragma unroll
+      for (int it = 0; it < kRItems; ++it) {
+        const uint64_t idx = base + (uint64_t)it * kRT + threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[it][k] = (idx < n && p.mask[k]) ? __ldg(in.c[k] + idx) : 0u;
+      }
+#pragma unroll
+      for (int it = 0; it < kRItems; ++it) {
+        const uint64_t idx = base + (uint64_t)it * kRT + threadIdx.x;
+        if (idx < n) atomicAdd(&h[digit_of<K>(v[it], p)], 1u);
+      }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < R; i += kRT) tile_hist[(uint64_t)i * ntiles + tile] = h[i];
