@@ -1541,7 +1541,6 @@ struct cdl_engine {
         log_x.insert(log_x.end(), h_est, h_est + kMlpIn);
         log_y.push_back((float)std::log2(1.0 + (double)size));
       };
-      bool predicted = false;
       if (predict) {
         // single pass into a buffer sized by the prediction; a batched one
         // sizes it from the host's bound on the cursor instead of reading it
@@ -1605,7 +1604,6 @@ struct cdl_engine {
             if (r != CDL_OK) return r;
             const uint64_t total = h_ctl[kSlotDirTotal];
             if (h_ctl[kSlotOverflow] == 0) {
-              predicted = true;
               ++est_pred;
               ++joins;
               log_sample(total);
@@ -1634,7 +1632,6 @@ struct cdl_engine {
           }
         }
       }
-      (void)predicted;
       // passes 1 and 2: counts, offsets, total
       DBuf off = alloc(std::max<uint64_t>(P.n, 1) * 8);
       DBuf ws = alloc(join_count_workspace(P.n));
