@@ -74,6 +74,40 @@ def test_struct_sizes_equal_the_c_compilers(tmp_path):
                    ctypes.sizeof(cdl.Atom), ctypes.sizeof(cdl.RuleS)]
 
 
+def test_field_offsets_equal_the_c_compilers(tmp_path):
+    """Every field of the ctypes mirrors of cdl_options, cdl_stats and
+    cdl_rule sits at the offset the C compiler gives the field of the same
+    name in include/cdl.h (two fields of one width declared in swapped
+    order keep the sizes equal but not the offsets)."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = [("cdl_options", cdl.Options), ("cdl_stats", cdl.Stats), ("cdl_rule", cdl.RuleS),
+               ("cdl_atom", cdl.Atom), ("cdl_term", cdl.Term)]
+    lines = []
+    want = []
+    for cname, py in mirrors:
+        for field in py._fields_:
+            name = field[0]
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {name}));')
+            want.append((cname, name, getattr(py, name).offset))
+    src = tmp_path / "offsets.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"cdl.h\"\n"
+                   "int main(void) {\n" + "\n".join(lines) + "\n  return 0;\n}\n")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    exe = tmp_path / "offsets"
+    r = subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], capture_output=True,
+                       text=True)
+    assert r.returncode == 0, r.stderr
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert len(got) == len(want)
+    for (cname, name, off), c_off in zip(want, got):
+        assert off == c_off, (cname, name, off, c_off)
+
+
 def test_header_is_plain_c(tmp_path):
     """include/cdl.h compiles as C99 (no C++ types in the boundary) and its
     declarations are usable from C."""
