@@ -163,9 +163,10 @@ typedef struct {
                            both atoms' hash indexes from each probe row and writes the head
                            tuples for every pair of matched rows (count pass: the product
                            of the two range lengths), so the table of the first join's
-                           results is never written; -1 = a chain of binary joins
-                           (Algorithm 1) throughout.  A probe row with 2^32 or more
-                           outputs raises CDL_E_CAPACITY.  Results never depend on it */
+                           results is never written (positive values act as 0); a
+                           negative value = a chain of binary joins (Algorithm 1)
+                           throughout.  A probe row with 2^32 or more outputs raises
+                           CDL_E_CAPACITY.  Results never depend on it */
 } cdl_options;
 
 /* Fills *opts with the defaults (everything zero / NULL except the
