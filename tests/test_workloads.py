@@ -55,3 +55,29 @@ def test_batched_sizes_log_uniform():
     s = W.batched_graph_sizes(512, 5)
     assert s.min() >= 1000 and s.max() <= 500000
     assert 0.3 < np.mean(np.log(s) < np.log(np.sqrt(1e3 * 5e5))) < 0.7
+
+
+def test_zipf_rank_frequencies():
+    """P(rank r) is r^-s / H(s): the frequencies of the hottest ranks
+    (through the permutation) match within sampling error."""
+    universe, s, count = 1000, 1.1, 400_000
+    perm = np.arange(universe, dtype=np.uint64)[::-1].copy()  # rank r -> id universe - r
+    ids = W.zipf_ids(count, universe, s, 9, 1, perm)
+    h = np.sum(np.arange(1, universe + 1, dtype=np.float64) ** -s)
+    for r in (1, 2, 10, 100):
+        p = r ** -s / h
+        got = np.count_nonzero(ids == universe - r) / count
+        assert abs(got - p) < 5 * np.sqrt(p * (1 - p) / count), (r, got, p)
+
+
+def test_forest_parents_uniform_below_the_child():
+    """Node i >= 1 draws its parent uniformly from [0, i): parent / i has
+    mean 1/2 and variance 1/12 over many nodes; cross edges have uniform
+    endpoints."""
+    n = 200_000
+    f = W.random_forest(n, 3)
+    tree, cross = f[: len(f) - n // 50], f[len(f) - n // 50:]
+    q = tree[:, 0].astype(np.float64) / tree[:, 1]
+    assert abs(q.mean() - 0.5) < 0.005 and abs(q.var() - 1 / 12) < 0.005
+    m = cross.astype(np.float64).mean(axis=0) / n
+    assert (abs(m - 0.5) < 0.03).all()
