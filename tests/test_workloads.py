@@ -81,3 +81,23 @@ def test_forest_parents_uniform_below_the_child():
     assert abs(q.mean() - 0.5) < 0.005 and abs(q.var() - 1 / 12) < 0.005
     m = cross.astype(np.float64).mean(axis=0) / n
     assert (abs(m - 0.5) < 0.03).all()
+
+
+def test_owl_schema_is_a_layered_dag():
+    """Every subclass edge goes one level up (so the subclass graph is a
+    DAG of the stated depth), every non-root class has one or two
+    parents, and subproperty edges go from a lower to a higher property."""
+    n_classes, levels, ne = 120, 12, 5000
+    _, sch = W.owl_triples(4000, 6, n_entities=ne, n_classes=n_classes, levels=levels)
+    lvl = (np.arange(n_classes) * levels) // n_classes
+    parents = {}
+    for c, d in sch.sub_class:
+        assert lvl[c - ne] == lvl[d - ne] + 1, (c, d)
+        parents.setdefault(c, set()).add(d)
+    for c in range(n_classes):
+        if lvl[c] > 0:
+            assert 1 <= len(parents.get(ne + c, ())) <= 2, c
+        else:
+            assert ne + c not in parents
+    assert all(a < b for a, b in sch.sub_prop) and len(set(sch.sub_prop)) == 40
+    assert not set(sch.transitive) & {p for pair in sch.inverse for p in pair}
